@@ -1,0 +1,273 @@
+/*
+ * lq.h -- C ABI of the GB300 (sm_103a) dense state-vector library for the
+ * method of arXiv 2512.23183 ("LogosQ").
+ *
+ * State vectors are caller-owned device buffers of 2^n complex128 amplitudes
+ * stored as interleaved (re, im) doubles (CUDA double2), the Complex64 dense
+ * state of Sec. II-B.  Qubit q is bit n-1-q of the amplitude index
+ * (MSB-first, Alg. 1 and Alg. 4).
+ *
+ * Conventions shared by every entry point:
+ *   - return an lq_status, never throw, never exit; on failure
+ *     lq_last_error() returns a message for the calling thread;
+ *   - device memory (states, scratch, workspaces) is owned by the caller and
+ *     never freed by the library; the library allocates no device memory;
+ *   - host arrays (gate lists, parameters, Pauli terms) are read during the
+ *     call only;
+ *   - work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
+ *     stream); calls are asynchronous unless they return host values, in which
+ *     case they synchronise `stream` before returning;
+ *   - sizes: 1 <= n <= 34 qubits.
+ *
+ * Validation stands in for the compile-time checks of Sec. III-B
+ * (parameter bounds, parametrised versus fixed gates):
+ *   LQ_ERR_INVALID_ARG for a qubit outside [0, n), a repeated qubit within a
+ *   gate, a parameter index >= np, a parameter on a fixed gate, a Pauli mask
+ *   with bits >= n, a NULL pointer where data is needed, or n out of range;
+ *   LQ_ERR_NONFINITE for NaN/Inf in parameters, angles, matrices or
+ *   coefficients (App. D: explicit error reporting instead of silent NaN).
+ */
+#ifndef LQ_API_H_
+#define LQ_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* lq_stream; /* == cudaStream_t */
+
+typedef enum {
+  LQ_OK = 0,
+  LQ_ERR_INVALID_ARG = 1,
+  LQ_ERR_UNSUPPORTED = 2,
+  LQ_ERR_NONFINITE = 3,
+  LQ_ERR_OOM = 4,       /* workspace / scratch smaller than required */
+  LQ_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+  LQ_ERR_TIMEOUT = 6    /* a bounded device-side wait gave up */
+} lq_status;
+
+/* Gate kinds.  Matrices are over the gate's listed qubits, the first listed
+ * qubit being the most significant bit of the local index (the two-qubit
+ * index (s1, s2) of Sec. II-C).  Controlled gates list their control(s)
+ * first.  Rotations are R_P(theta) = exp(-i theta sigma_P / 2) (Sec. III-A). */
+typedef enum {
+  LQ_H = 0,   /* Hadamard [[1,1],[1,-1]]/sqrt2 (App. C)                     */
+  LQ_X,       /* Pauli X                                                     */
+  LQ_Y,       /* Pauli Y [[0,-i],[i,0]]                                      */
+  LQ_Z,       /* Pauli Z                                                     */
+  LQ_S,       /* diag(1, i)                                                  */
+  LQ_SDG,     /* diag(1, -i)                                                 */
+  LQ_T,       /* diag(1, e^{i pi/4})                                         */
+  LQ_TDG,     /* diag(1, e^{-i pi/4})                                        */
+  LQ_RX,      /* exp(-i theta X/2)                                           */
+  LQ_RY,      /* exp(-i theta Y/2)                                           */
+  LQ_RZ,      /* exp(-i theta Z/2)                                           */
+  LQ_P,       /* diag(1, e^{i theta})                                        */
+  LQ_U1,      /* 2x2 unitary in mat[0..7]                                    */
+  LQ_CNOT,    /* Alg. 1: (control, target)                                   */
+  LQ_CY,      /* controlled Y                                                */
+  LQ_CZ,      /* diag(1,1,1,-1)                                              */
+  LQ_CP,      /* diag(1,1,1,e^{i theta}), the controlled phase of Alg. 3     */
+  LQ_SWAP,    /* Alg. 3 swaps                                                */
+  LQ_CRX,     /* |0><0| (x) I + |1><1| (x) RX(theta)                         */
+  LQ_CRY,     /* |0><0| (x) I + |1><1| (x) RY(theta) (App. D circuit)        */
+  LQ_CRZ,     /* |0><0| (x) I + |1><1| (x) RZ(theta)                         */
+  LQ_RXX,     /* exp(-i theta X(x)X / 2) (Sec. VII-A Trotter gates)          */
+  LQ_RYY,     /* exp(-i theta Y(x)Y / 2)                                     */
+  LQ_RZZ,     /* exp(-i theta Z(x)Z / 2)                                     */
+  LQ_CCX,     /* Toffoli, Alg. 4: (control1, control2, target)               */
+  LQ_U2,      /* 4x4 unitary in mat[0..31]                                   */
+  LQ_GATE_KIND_COUNT
+} lq_gate_kind;
+
+/* One operation of a circuit (the Operation/Circuit of Sec. II-A flattened
+ * into plain data).  The angle used is params[param] + angle when
+ * param >= 0, else the fixed angle.  mat holds row-major (re, im) pairs for
+ * LQ_U1 (8 doubles) and LQ_U2 (32 doubles). */
+typedef struct {
+  int32_t kind;
+  int32_t qubits[3];
+  int32_t param;
+  int32_t reserved;
+  double angle;
+  double mat[32];
+} lq_gate;
+
+/* One term c * P of a Pauli sum H = sum_t c_t P_t (Sec. VI-A).  P acts on the
+ * index as P|s> = i^{ny} (-1)^{popcount(s & zmask)} |s ^ xmask>, where bit b
+ * of xmask (zmask) is set when the qubit n-1-b carries X or Y (Z or Y) and
+ * ny counts the Y factors (popcount(xmask & zmask)). */
+typedef struct {
+  double coeff;
+  uint64_t xmask;
+  uint64_t zmask;
+} lq_pauli_term;
+
+/* Gradient methods of lq_param_shift_grad. */
+typedef enum {
+  LQ_PSR_PLAIN = 0,   /* 2P+1 separate circuit runs, as ParameterShift does  */
+  LQ_PSR_BATCHED = 1  /* all shifted circuits in one persistent launch        */
+} lq_psr_method;
+
+/* QFT methods of lq_qft. */
+typedef enum {
+  LQ_QFT_FFT = 0,   /* Alg. 2: inverse FFT / sqrt(N) */
+  LQ_QFT_GATES = 1  /* Alg. 3: H, CP(pi/2^(j-i)), SWAP on the dense state */
+} lq_qft_method;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lq_last_error(void);
+
+/* Library version string. */
+const char* lq_version(void);
+
+/* Parse a Pauli string (character q acts on qubit q; one of I X Y Z, length
+ * n) into a term.  Host only. */
+lq_status lq_pauli_from_string(const char* s, int n, double coeff, lq_pauli_term* out);
+
+/* |basis>: amplitude `basis` = 1, all others 0 (DenseState::zero_state,
+ * Sec. II-B, for basis = 0).  amps: device, 2^n double2. */
+lq_status lq_state_init(void* amps, int n, uint64_t basis, lq_stream stream);
+
+/* Apply the circuit in list order (Circuit::execute, Sec. II-A) in place.
+ * gates: host array of ng gates; params: host array of np doubles (may be
+ * NULL when np == 0).  Each gate is a direct bitwise update of amplitude
+ * pairs or quads (Sec. IV-A, Alg. 1, Alg. 4); gates are grouped into
+ * shared-memory tile passes so each pass reads and writes the state once. */
+lq_status lq_apply_circuit(void* amps, int n, const lq_gate* gates, int ng,
+                           const double* params, int np, lq_stream stream);
+
+/* QFT|x> = N^{-1/2} sum_k e^{2 pi i x k / N} |k> (Sec. IV-B) in place;
+ * inverse = 1 applies the inverse QFT.  method LQ_QFT_FFT follows Alg. 2,
+ * LQ_QFT_GATES follows Alg. 3.  Neither method needs scratch: pass NULL/0. */
+lq_status lq_qft(void* amps, int n, int inverse, int method, void* scratch,
+                 size_t scratch_bytes, lq_stream stream);
+
+/* Bytes of device workspace lq_expval_pauli_sum needs. */
+size_t lq_expval_workspace_size(int n, int nt);
+
+/* E = sum_t c_t Re <psi|P_t|psi> (Sec. VI-A, Sec. VII-A-2) for the state in
+ * `amps` (device, read only).  out: host double; the call synchronises
+ * `stream`.  workspace: device, >= lq_expval_workspace_size(n, nt) bytes. */
+lq_status lq_expval_pauli_sum(const void* amps, int n, const lq_pauli_term* terms, int nt,
+                              double* out, void* workspace, size_t ws_bytes,
+                              lq_stream stream);
+
+/* Same, asynchronous: the result is written to the device double out_dev. */
+lq_status lq_expval_pauli_sum_async(const void* amps, int n, const lq_pauli_term* terms,
+                                    int nt, double* out_dev, void* workspace,
+                                    size_t ws_bytes, lq_stream stream);
+
+/* out = H psi for H = sum_t c_t P_t (device buffers, out != in). */
+lq_status lq_apply_pauli_sum(void* out, const void* in, int n, const lq_pauli_term* terms,
+                             int nt, lq_stream stream);
+
+/* Bytes of device workspace lq_param_shift_grad needs for this problem. */
+size_t lq_param_shift_workspace_size(int n, int np, int nt, int method);
+
+/* Energy E(theta) and its parameter-shift gradient (Eq. parameter_shift,
+ * s = pi/2; ParameterShift::compute_gradient of Sec. III-C):
+ *   grad[i] = ( E(theta + s e_i) - E(theta - s e_i) ) / 2,
+ * every evaluation starting from |0...0>.  Every parameter must drive exactly
+ * one gate whose generator has two eigenvalues one apart (RX, RY, RZ, P, CP,
+ * RXX, RYY, RZZ), else LQ_ERR_UNSUPPORTED (controlled rotations need the
+ * four-term rule, see lq_param_shift_grad_general).  energy: host double;
+ * grad: host array of np doubles; the call synchronises `stream`. */
+lq_status lq_param_shift_grad(int n, const lq_gate* gates, int ng, const double* params,
+                              int np, const lq_pauli_term* terms, int nt, int method,
+                              double* energy, double* grad, void* workspace,
+                              size_t ws_bytes, lq_stream stream);
+
+/* Generalised shift rules: a parameter may drive several gates (the
+ * derivative sums the per-occurrence shifts) and controlled rotations
+ * CRX/CRY/CRZ use the four-term rule with shifts pi/2 and 3pi/2 and weights
+ * (sqrt2 +- 1) / (4 sqrt2) (the generalised rules cited in Sec. III-A).
+ * Always batched. */
+size_t lq_param_shift_general_workspace_size(int n, const lq_gate* gates, int ng,
+                                             int np, int nt);
+lq_status lq_param_shift_grad_general(int n, const lq_gate* gates, int ng,
+                                      const double* params, int np,
+                                      const lq_pauli_term* terms, int nt, double* energy,
+                                      double* grad, void* workspace, size_t ws_bytes,
+                                      lq_stream stream);
+
+/* Bytes of device workspace lq_adjoint_grad needs. */
+size_t lq_adjoint_workspace_size(int n, int ng, int np, int nt);
+
+/* Energy and exact gradient by reverse-mode (adjoint) differentiation: the
+ * state psi_L = U_L...U_1|0>, lambda = H psi_L, then for k = L..1
+ * grad[param(k)] += d/dtheta <psi|H|psi> through gate k, computed from
+ * <lambda_k| dU_k |psi_{k-1}>, with psi_{k-1} = U_k^dag psi_k and
+ * lambda_{k-1} = U_k^dag lambda_k.  Holds two states; any parametrised gate
+ * kind is allowed and a parameter may drive several gates.  energy/grad:
+ * host; the call synchronises `stream`. */
+lq_status lq_adjoint_grad(int n, const lq_gate* gates, int ng, const double* params, int np,
+                          const lq_pauli_term* terms, int nt, double* energy, double* grad,
+                          void* workspace, size_t ws_bytes, lq_stream stream);
+
+/* First-order Trotter-Suzuki evolution (Eq. trotter, Sec. VII-A):
+ *   H(t) = sum_k c_k P_k + h(t) sum_f d_f F_f,  h(t) = A sin(omega t),
+ * `steps` steps of dt; step j applies exp(-i c_k P_k dt) for the static
+ * terms in order, then exp(-i h(t_j) d_f F_f dt) for the field terms in
+ * order, t_j = j dt.  In place on `amps`. */
+lq_status lq_trotter_evolve(void* amps, int n, const lq_pauli_term* terms, int nt,
+                            const lq_pauli_term* field, int nf, double A, double omega,
+                            double dt, int steps, lq_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Plans: what a call will launch, for measurement and tuning.  FP64 flops
+ * count what the kernels execute (FMA = 2 flops, in the forms the library
+ * uses: tangent-form rotations, deferred scalars); dram_bytes is the minimal
+ * traffic of the launches (each tile pass reads and writes the state once:
+ * 32 * 2^n bytes).
+ */
+typedef struct {
+  int32_t npasses;      /* kernel launches of the state-vector passes */
+  int32_t tile_bits;    /* tile width k of the passes (max over passes) */
+  double dp_flops;      /* FP64 flops executed */
+  double dram_bytes;    /* minimal DRAM bytes moved */
+} lq_plan_info;
+
+/* Plan of lq_apply_circuit for this circuit (host only, no GPU needed). */
+lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* params, int np,
+                          lq_plan_info* out);
+
+/* Plan of lq_qft (host only). */
+lq_status lq_qft_plan(int n, int method, lq_plan_info* out);
+
+/* ---------------------------------------------------------------------------
+ * Uneven batches: many independent problems (each its own n, circuit and
+ * Hamiltonian) in one persistent launch.  Problems are described by
+ * lq_problem; results go to host arrays.
+ */
+typedef struct {
+  int32_t n;
+  int32_t ng;
+  int32_t np;
+  int32_t nt;
+  int32_t want_grad;            /* 0: energy only; 1: energy and gradient */
+  int32_t reserved;
+  const lq_gate* gates;         /* host */
+  const double* params;         /* host */
+  const lq_pauli_term* terms;   /* host */
+  double* energy;               /* host out */
+  double* grad;                 /* host out (np doubles) when want_grad */
+} lq_problem;
+
+/* Device workspace needed to run `count` problems in one batched launch. */
+size_t lq_batch_workspace_size(const lq_problem* problems, int count);
+
+/* Run every problem's 2P+1 (or 1, energy only) circuits in one persistent
+ * launch and write the energies/gradients.  Same gate restrictions as
+ * lq_param_shift_grad.  Synchronises `stream`. */
+lq_status lq_batch_param_shift(const lq_problem* problems, int count, void* workspace,
+                               size_t ws_bytes, lq_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQ_API_H_ */

@@ -1,0 +1,373 @@
+"""Python binding of liblq, the sm_103a state-vector library of include/lq.h.
+
+Argument marshalling only: gate lists and Pauli sums are packed into the C
+structs of the ABI, torch tensors supply device memory and streams, and every
+step of the computation runs in the library's CUDA kernels.  There is no CPU
+fallback: if liblq.so cannot be loaded, ``lib()`` raises.
+
+Gates are any objects with fields ``name, qubits, param, angle, mat`` (for
+example ``workloads.Gate``); Pauli sums are lists of ``(coeff, "XYZI...")``
+with character q acting on qubit q (qubit 0 = most significant index bit).
+States are contiguous ``torch.complex128`` CUDA tensors of 2^n amplitudes.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblq.so")
+
+c_int32, c_uint64, c_double, c_size_t = ctypes.c_int32, ctypes.c_uint64, ctypes.c_double, ctypes.c_size_t
+c_void_p = ctypes.c_void_p
+
+
+class LqGate(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("qubits", c_int32 * 3), ("param", c_int32),
+                ("reserved", c_int32), ("angle", c_double), ("mat", c_double * 32)]
+
+
+class LqPauliTerm(ctypes.Structure):
+    _fields_ = [("coeff", c_double), ("xmask", c_uint64), ("zmask", c_uint64)]
+
+
+class LqPlanInfo(ctypes.Structure):
+    _fields_ = [("npasses", c_int32), ("tile_bits", c_int32), ("dp_flops", c_double),
+                ("dram_bytes", c_double)]
+
+
+class LqProblem(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("ng", c_int32), ("np", c_int32), ("nt", c_int32),
+                ("want_grad", c_int32), ("reserved", c_int32),
+                ("gates", ctypes.POINTER(LqGate)), ("params", ctypes.POINTER(c_double)),
+                ("terms", ctypes.POINTER(LqPauliTerm)), ("energy", ctypes.POINTER(c_double)),
+                ("grad", ctypes.POINTER(c_double))]
+
+
+# lq_gate_kind values of include/lq.h
+KINDS = {name: i for i, name in enumerate(
+    "H X Y Z S SDG T TDG RX RY RZ P U1 CNOT CY CZ CP SWAP CRX CRY CRZ RXX RYY RZZ CCX U2".split())}
+
+STATUS = {0: "LQ_OK", 1: "LQ_ERR_INVALID_ARG", 2: "LQ_ERR_UNSUPPORTED", 3: "LQ_ERR_NONFINITE",
+          4: "LQ_ERR_OOM", 5: "LQ_ERR_CUDA", 6: "LQ_ERR_TIMEOUT"}
+PSR_PLAIN, PSR_BATCHED = 0, 1
+QFT_FFT, QFT_GATES = 0, 1
+
+
+class LqError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+EXPORTS = [
+    "lq_last_error", "lq_version", "lq_pauli_from_string", "lq_state_init", "lq_apply_circuit",
+    "lq_qft", "lq_expval_workspace_size", "lq_expval_pauli_sum", "lq_expval_pauli_sum_async",
+    "lq_apply_pauli_sum", "lq_param_shift_workspace_size", "lq_param_shift_grad",
+    "lq_param_shift_general_workspace_size", "lq_param_shift_grad_general",
+    "lq_adjoint_workspace_size", "lq_adjoint_grad", "lq_trotter_evolve",
+    "lq_batch_workspace_size", "lq_batch_param_shift", "lq_circuit_plan", "lq_qft_plan",
+]
+
+
+def load(build_if_missing=True):
+    """Load liblq.so (building it in-tree with nvcc when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise ImportError("liblq.so is missing; run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER
+    L.lq_last_error.restype = ctypes.c_char_p
+    L.lq_version.restype = ctypes.c_char_p
+    L.lq_pauli_from_string.argtypes = [ctypes.c_char_p, ctypes.c_int, c_double, P(LqPauliTerm)]
+    L.lq_state_init.argtypes = [c_void_p, ctypes.c_int, c_uint64, c_void_p]
+    L.lq_apply_circuit.argtypes = [c_void_p, ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double),
+                                   ctypes.c_int, c_void_p]
+    L.lq_qft.argtypes = [c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, c_void_p, c_size_t,
+                         c_void_p]
+    L.lq_expval_workspace_size.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.lq_expval_workspace_size.restype = c_size_t
+    L.lq_expval_pauli_sum.argtypes = [c_void_p, ctypes.c_int, P(LqPauliTerm), ctypes.c_int,
+                                      P(c_double), c_void_p, c_size_t, c_void_p]
+    L.lq_expval_pauli_sum_async.argtypes = [c_void_p, ctypes.c_int, P(LqPauliTerm), ctypes.c_int,
+                                            c_void_p, c_void_p, c_size_t, c_void_p]
+    L.lq_apply_pauli_sum.argtypes = [c_void_p, c_void_p, ctypes.c_int, P(LqPauliTerm),
+                                     ctypes.c_int, c_void_p]
+    L.lq_param_shift_workspace_size.argtypes = [ctypes.c_int] * 4
+    L.lq_param_shift_workspace_size.restype = c_size_t
+    L.lq_param_shift_grad.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double),
+                                      ctypes.c_int, P(LqPauliTerm), ctypes.c_int, ctypes.c_int,
+                                      P(c_double), P(c_double), c_void_p, c_size_t, c_void_p]
+    L.lq_param_shift_general_workspace_size.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int,
+                                                        ctypes.c_int, ctypes.c_int]
+    L.lq_param_shift_general_workspace_size.restype = c_size_t
+    L.lq_param_shift_grad_general.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double),
+                                              ctypes.c_int, P(LqPauliTerm), ctypes.c_int,
+                                              P(c_double), P(c_double), c_void_p, c_size_t,
+                                              c_void_p]
+    L.lq_adjoint_workspace_size.argtypes = [ctypes.c_int] * 4
+    L.lq_adjoint_workspace_size.restype = c_size_t
+    L.lq_adjoint_grad.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double),
+                                  ctypes.c_int, P(LqPauliTerm), ctypes.c_int, P(c_double),
+                                  P(c_double), c_void_p, c_size_t, c_void_p]
+    L.lq_trotter_evolve.argtypes = [c_void_p, ctypes.c_int, P(LqPauliTerm), ctypes.c_int,
+                                    P(LqPauliTerm), ctypes.c_int, c_double, c_double, c_double,
+                                    ctypes.c_int, c_void_p]
+    L.lq_batch_workspace_size.argtypes = [P(LqProblem), ctypes.c_int]
+    L.lq_batch_workspace_size.restype = c_size_t
+    L.lq_batch_param_shift.argtypes = [P(LqProblem), ctypes.c_int, c_void_p, c_size_t, c_void_p]
+    L.lq_circuit_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
+                                  P(LqPlanInfo)]
+    L.lq_qft_plan.argtypes = [ctypes.c_int, ctypes.c_int, P(LqPlanInfo)]
+    _lib = L
+    return L
+
+
+lib = load
+
+
+def _check(st):
+    if st != 0:
+        raise LqError(st, load().lq_last_error().decode())
+
+
+def version():
+    return load().lq_version().decode()
+
+
+# ------------------------------------------------------------- marshalling
+
+def pack_gates(gates):
+    arr = (LqGate * max(len(gates), 1))()
+    for i, g in enumerate(gates):
+        G = arr[i]
+        G.kind = KINDS[g.name]
+        q = list(g.qubits) + [-1] * (3 - len(g.qubits))
+        for j in range(3):
+            G.qubits[j] = q[j]
+        G.param = g.param
+        G.angle = g.angle
+        if g.mat is not None:
+            m = np.ascontiguousarray(np.asarray(g.mat, np.complex128).reshape(-1)).view(np.float64)
+            for j, v in enumerate(m):
+                G.mat[j] = float(v)
+    return arr
+
+
+def pack_terms(terms, n):
+    arr = (LqPauliTerm * max(len(terms), 1))()
+    L = load()
+    for i, (c, s) in enumerate(terms):
+        _check(L.lq_pauli_from_string(s.encode(), n, float(c), ctypes.byref(arr[i])))
+    return arr
+
+
+def _params(params):
+    p = np.ascontiguousarray(np.asarray(params if params is not None else [], np.float64))
+    return p, p.ctypes.data_as(ctypes.POINTER(c_double)), int(p.size)
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_state(amps, n):
+    import torch
+
+    if not (amps.is_cuda and amps.dtype == torch.complex128 and amps.is_contiguous()):
+        raise ValueError("state must be a contiguous complex128 CUDA tensor")
+    if amps.numel() != (1 << n):
+        raise ValueError("state has %d amplitudes, expected 2^%d" % (amps.numel(), n))
+
+
+def _workspace(nbytes, device):
+    import torch
+
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# --------------------------------------------------------------- entry points
+
+def new_state(n, basis=0, device="cuda", stream=None):
+    import torch
+
+    amps = torch.empty(1 << n, dtype=torch.complex128, device=device)
+    state_init(amps, n, basis, stream)
+    return amps
+
+
+def state_init(amps, n, basis=0, stream=None):
+    _check_state(amps, n)
+    _check(load().lq_state_init(_ptr(amps), n, int(basis), _stream(stream)))
+    return amps
+
+
+def apply_circuit(amps, n, gates, params=None, stream=None):
+    _check_state(amps, n)
+    g = pack_gates(gates)
+    p, pp, np_ = _params(params)
+    _check(load().lq_apply_circuit(_ptr(amps), n, g, len(gates), pp, np_, _stream(stream)))
+    return amps
+
+
+def qft(amps, n, inverse=False, method=QFT_FFT, stream=None):
+    _check_state(amps, n)
+    _check(load().lq_qft(_ptr(amps), n, int(inverse), int(method), None, 0, _stream(stream)))
+    return amps
+
+
+def expval_pauli_sum(amps, n, terms, stream=None, workspace=None):
+    _check_state(amps, n)
+    L = load()
+    t = pack_terms(terms, n)
+    need = L.lq_expval_workspace_size(n, len(terms))
+    ws = workspace if workspace is not None else _workspace(need, amps.device)
+    out = c_double(0.0)
+    _check(L.lq_expval_pauli_sum(_ptr(amps), n, t, len(terms), ctypes.byref(out), _ptr(ws),
+                                 ws.numel(), _stream(stream)))
+    return out.value
+
+
+def apply_pauli_sum(out, amps, n, terms, stream=None):
+    _check_state(amps, n)
+    _check_state(out, n)
+    t = pack_terms(terms, n)
+    _check(load().lq_apply_pauli_sum(_ptr(out), _ptr(amps), n, t, len(terms), _stream(stream)))
+    return out
+
+
+def param_shift_grad(n, gates, params, terms, method=PSR_BATCHED, device="cuda", stream=None,
+                     workspace=None):
+    """(E, grad) by the parameter-shift rule (two-term rule, single-use
+    parameters)."""
+    L = load()
+    g = pack_gates(gates)
+    t = pack_terms(terms, n)
+    p, pp, np_ = _params(params)
+    need = L.lq_param_shift_workspace_size(n, np_, len(terms), int(method))
+    ws = workspace if workspace is not None else _workspace(need, device)
+    e = c_double(0.0)
+    grad = np.zeros(max(np_, 1))
+    _check(L.lq_param_shift_grad(n, g, len(gates), pp, np_, t, len(terms), int(method),
+                                 ctypes.byref(e), grad.ctypes.data_as(ctypes.POINTER(c_double)),
+                                 _ptr(ws), ws.numel(), _stream(stream)))
+    return e.value, grad[:np_].copy()
+
+
+def param_shift_grad_general(n, gates, params, terms, device="cuda", stream=None):
+    """(E, grad) with shared parameters and four-term rules for controlled
+    rotations."""
+    L = load()
+    g = pack_gates(gates)
+    t = pack_terms(terms, n)
+    p, pp, np_ = _params(params)
+    need = L.lq_param_shift_general_workspace_size(n, g, len(gates), np_, len(terms))
+    ws = _workspace(need, device)
+    e = c_double(0.0)
+    grad = np.zeros(max(np_, 1))
+    _check(L.lq_param_shift_grad_general(n, g, len(gates), pp, np_, t, len(terms), ctypes.byref(e),
+                                         grad.ctypes.data_as(ctypes.POINTER(c_double)), _ptr(ws),
+                                         ws.numel(), _stream(stream)))
+    return e.value, grad[:np_].copy()
+
+
+def adjoint_grad(n, gates, params, terms, device="cuda", stream=None, workspace=None):
+    """(E, grad) by reverse-mode (adjoint) differentiation."""
+    L = load()
+    g = pack_gates(gates)
+    t = pack_terms(terms, n)
+    p, pp, np_ = _params(params)
+    need = L.lq_adjoint_workspace_size(n, len(gates), np_, len(terms))
+    ws = workspace if workspace is not None else _workspace(need, device)
+    e = c_double(0.0)
+    grad = np.zeros(max(np_, 1))
+    _check(L.lq_adjoint_grad(n, g, len(gates), pp, np_, t, len(terms), ctypes.byref(e),
+                             grad.ctypes.data_as(ctypes.POINTER(c_double)), _ptr(ws), ws.numel(),
+                             _stream(stream)))
+    return e.value, grad[:np_].copy()
+
+
+def trotter_evolve(amps, n, terms, field_terms, A, omega, dt, steps, stream=None):
+    _check_state(amps, n)
+    t = pack_terms(terms, n)
+    f = pack_terms(field_terms, n)
+    _check(load().lq_trotter_evolve(_ptr(amps), n, t, len(terms), f, len(field_terms), float(A),
+                                    float(omega), float(dt), int(steps), _stream(stream)))
+    return amps
+
+
+def circuit_plan(n, gates, params=None):
+    """dict(npasses, tile_bits, dp_flops, dram_bytes) of lq_apply_circuit."""
+    g = pack_gates(gates)
+    p, pp, np_ = _params(params)
+    info = LqPlanInfo()
+    _check(load().lq_circuit_plan(n, g, len(gates), pp, np_, ctypes.byref(info)))
+    return dict(npasses=info.npasses, tile_bits=info.tile_bits, dp_flops=info.dp_flops,
+                dram_bytes=info.dram_bytes)
+
+
+def qft_plan(n, method=QFT_FFT):
+    info = LqPlanInfo()
+    _check(load().lq_qft_plan(n, int(method), ctypes.byref(info)))
+    return dict(npasses=info.npasses, tile_bits=info.tile_bits, dp_flops=info.dp_flops,
+                dram_bytes=info.dram_bytes)
+
+
+class BatchProblem:
+    """One problem of an uneven batch: its circuit, parameters and Pauli sum."""
+
+    def __init__(self, n, gates, params, terms, want_grad=True):
+        self.n, self.gates, self.terms, self.want_grad = n, gates, terms, want_grad
+        self.params = np.ascontiguousarray(np.asarray(params, np.float64))
+        self.energy = None
+        self.grad = None
+
+
+def batch_param_shift(problems, device="cuda", stream=None, workspace=None):
+    """Run many (n, circuit, H) problems' parameter-shift circuits in one
+    batched launch; fills problem.energy / problem.grad."""
+    L = load()
+    arr = (LqProblem * len(problems))()
+    keep = []
+    for i, pb in enumerate(problems):
+        g = pack_gates(pb.gates)
+        t = pack_terms(pb.terms, pb.n)
+        e = np.zeros(1)
+        gr = np.zeros(max(pb.params.size, 1))
+        keep.append((g, t, e, gr, pb.params))
+        P = arr[i]
+        P.n, P.ng, P.np, P.nt = pb.n, len(pb.gates), pb.params.size, len(pb.terms)
+        P.want_grad = int(pb.want_grad)
+        P.gates = g
+        P.params = pb.params.ctypes.data_as(ctypes.POINTER(c_double))
+        P.terms = t
+        P.energy = e.ctypes.data_as(ctypes.POINTER(c_double))
+        P.grad = gr.ctypes.data_as(ctypes.POINTER(c_double))
+    need = L.lq_batch_workspace_size(arr, len(problems))
+    ws = workspace if workspace is not None else _workspace(need, device)
+    _check(L.lq_batch_param_shift(arr, len(problems), _ptr(ws), ws.numel(), _stream(stream)))
+    for pb, (g, t, e, gr, _) in zip(problems, keep):
+        pb.energy = float(e[0])
+        pb.grad = gr[: pb.params.size].copy()
+    return problems
+
+
+from .autograd import AdjointEnergy, energy  # noqa: E402,F401

@@ -1,0 +1,301 @@
+// lq_api.cu -- the extern "C" entry points declared in include/lq.h:
+// argument validation, lowering/scheduling on the host, kernel launches on
+// the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "lq_coefs.h"
+#include "lq_internal.h"
+#include "lq_kernels.h"
+
+namespace lq {
+
+const char* last_error();
+void clear_error();
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 1;
+  }
+  return cached[dev];
+}
+
+#define LQ_CUDA(expr)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(LQ_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                           \
+  } while (0)
+
+static inline std::size_t align256(std::size_t b) { return (b + 255) & ~(std::size_t)255; }
+
+// ------------------------------------------------------- Pauli-term chunks
+
+int exp_chunk_count(const lq_pauli_term* terms, int nt) {
+  std::map<uint64_t, int> groups;
+  for (int t = 0; t < nt; t++) groups[terms[t].xmask]++;
+  int chunks = 1, g = 0, c = 0;
+  for (auto& kv : groups) {
+    int left = kv.second;
+    while (left > 0) {
+      if (g == EXP_MAX_GROUPS || c == EXP_MAX_TERMS) {
+        chunks++;
+        g = 0;
+        c = 0;
+      }
+      int take = left < EXP_MAX_TERMS - c ? left : EXP_MAX_TERMS - c;
+      g++;
+      c += take;
+      left -= take;
+    }
+  }
+  return chunks;
+}
+
+int build_exp_chunks(int n, const lq_pauli_term* terms, int nt, ExpParams* chunks,
+                     int max_chunks) {
+  std::map<uint64_t, std::vector<int>> groups;
+  for (int t = 0; t < nt; t++) groups[terms[t].xmask].push_back(t);
+  int ci = 0;
+  std::memset(&chunks[0], 0, sizeof(ExpParams));
+  chunks[0].n = n;
+  for (auto& kv : groups) {
+    const uint64_t x = kv.first;
+    std::size_t done = 0;
+    while (done < kv.second.size()) {
+      ExpParams* E = &chunks[ci];
+      int used = 0;
+      for (int g = 0; g < E->ngroups; g++) used += E->groups[g].count;
+      if (E->ngroups == EXP_MAX_GROUPS || used == EXP_MAX_TERMS) {
+        if (++ci >= max_chunks) return -1;
+        E = &chunks[ci];
+        std::memset(E, 0, sizeof(ExpParams));
+        E->n = n;
+        used = 0;
+      }
+      ExpGroup& G = E->groups[E->ngroups++];
+      G.x = x;
+      G.h = x ? 63 - __builtin_clzll(x) : 0;
+      G.first = used;
+      G.count = 0;
+      while (done < kv.second.size() && used < EXP_MAX_TERMS) {
+        const lq_pauli_term& P = terms[kv.second[done++]];
+        ExpTerm& T = E->terms[used++];
+        T.c = P.coeff;
+        T.c2 = 2.0 * P.coeff;
+        T.z = P.zmask;
+        T.k0 = __builtin_popcountll(P.xmask & P.zmask) & 3;
+        G.count++;
+      }
+    }
+  }
+  return ci + 1;
+}
+
+// <H> of nstates states (stride apart) into out_dev[0..nstates).  partial:
+// expval_grid(n) * nstates doubles.
+lq_status expval_states(const double2* states, uint64_t stride, int nstates, int n,
+                               const lq_pauli_term* terms, int nt, double* partial,
+                               double* out_dev, cudaStream_t s) {
+  if (nt == 0) {
+    LQ_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(double) * nstates, s));
+    return LQ_OK;
+  }
+  int nch = exp_chunk_count(terms, nt);
+  std::vector<ExpParams> ch((std::size_t)nch);
+  int got = build_exp_chunks(n, terms, nt, ch.data(), nch);
+  if (got < 0) return fail(LQ_ERR_INVALID_ARG, "internal: term chunking");
+  for (int c = 0; c < got; c++)
+    LQ_CUDA(launch_expval(ch[c], states, stride, nstates, partial, out_dev, c > 0, s));
+  return LQ_OK;
+}
+
+// Run a lowered op list on nstates states; flags of the first pass may ask
+// for a |0...0> start.
+static lq_status run_ops(double2* states, uint64_t stride, int nstates, int n, const LOp* ops,
+                         std::size_t nops, double zr, double zi, bool init_zero,
+                         cudaStream_t s) {
+  ScheduleOptions opt;
+  Schedule S;
+  lq_status st = schedule_ops(n, ops, nops, zr, zi, opt, S);
+  if (st) return st;
+  if (S.npasses == 0) {
+    if (init_zero)
+      for (int i = 0; i < nstates; i++)
+        LQ_CUDA(launch_init_basis(states + (uint64_t)i * stride, n, 0, s));
+    return LQ_OK;
+  }
+  for (int p = 0; p < S.npasses; p++) {
+    if (p == 0 && init_zero) S.passes[p].h.flags |= PF_INIT_ZERO;
+    LQ_CUDA(launch_pass(S.passes[p], states, stride, nstates, s));
+  }
+  return LQ_OK;
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char* lq_last_error(void) { return lq::last_error(); }
+
+const char* lq_version(void) { return "lq 0.1 (sm_103a)"; }
+
+lq_status lq_pauli_from_string(const char* s, int n, double coeff, lq_pauli_term* out) {
+  if (!s || !out) return fail(LQ_ERR_INVALID_ARG, "NULL argument");
+  lq_status st = check_n(n);
+  if (st) return st;
+  if ((int)std::strlen(s) != n) return fail(LQ_ERR_INVALID_ARG, "Pauli string length != n");
+  if (!std::isfinite(coeff)) return fail(LQ_ERR_NONFINITE, "coefficient not finite");
+  uint64_t x = 0, z = 0;
+  for (int q = 0; q < n; q++) {
+    uint64_t b = 1ull << (n - 1 - q);
+    switch (s[q]) {
+      case 'I': break;
+      case 'X': x |= b; break;
+      case 'Y': x |= b; z |= b; break;
+      case 'Z': z |= b; break;
+      default: return fail(LQ_ERR_INVALID_ARG, "bad Pauli character '%c'", s[q]);
+    }
+  }
+  out->coeff = coeff;
+  out->xmask = x;
+  out->zmask = z;
+  return LQ_OK;
+}
+
+lq_status lq_state_init(void* amps, int n, uint64_t basis, lq_stream stream) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!amps) return fail(LQ_ERR_INVALID_ARG, "amps is NULL");
+  if (basis >> n) return fail(LQ_ERR_INVALID_ARG, "basis index >= 2^n");
+  LQ_CUDA(launch_init_basis((double2*)amps, n, basis, (cudaStream_t)stream));
+  return LQ_OK;
+}
+
+lq_status lq_apply_circuit(void* amps, int n, const lq_gate* gates, int ng,
+                           const double* params, int np, lq_stream stream) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!amps) return fail(LQ_ERR_INVALID_ARG, "amps is NULL");
+  LOp* ops = nullptr;
+  std::size_t nops = 0;
+  double zr, zi;
+  st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi);
+  if (st) return st;
+  st = run_ops((double2*)amps, 0, 1, n, ops, nops, zr, zi, false, (cudaStream_t)stream);
+  delete[] ops;
+  return st;
+}
+
+lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* params, int np,
+                          lq_plan_info* out) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
+  LOp* ops = nullptr;
+  std::size_t nops = 0;
+  double zr, zi;
+  st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi);
+  if (st) return st;
+  ScheduleOptions opt;
+  Schedule S;
+  st = schedule_ops(n, ops, nops, zr, zi, opt, S);
+  delete[] ops;
+  if (st) return st;
+  out->npasses = S.npasses;
+  out->tile_bits = S.npasses ? S.passes[0].h.k : 0;
+  double fl = 0;
+  for (int p = 0; p < S.npasses; p++) {
+    const PassParams& P = S.passes[p];
+    for (int o = 0; o < P.h.nops; o++) {
+      const Op& d = P.ops[o];
+      LOp l;
+      l.type = d.type;
+      l.mode = d.mode;
+      // condition width: tile-local and CTA bits together
+      uint64_t cmbits = (uint64_t)__builtin_popcountll(d.cm_glob) + __builtin_popcount(d.cm_loc);
+      l.cm = cmbits ? ((1ull << cmbits) - 1) : 0;
+      fl += op_flops(l, n);
+    }
+  }
+  out->dp_flops = fl;
+  out->dram_bytes = 32.0 * std::ldexp(1.0, n) * S.npasses;
+  return LQ_OK;
+}
+
+size_t lq_expval_workspace_size(int n, int nt) {
+  (void)nt;
+  if (n < 1 || n > 34) return 0;
+  return align256(sizeof(double)) + align256(sizeof(double) * (std::size_t)expval_grid(n));
+}
+
+lq_status lq_expval_pauli_sum_async(const void* amps, int n, const lq_pauli_term* terms,
+                                    int nt, double* out_dev, void* workspace,
+                                    size_t ws_bytes, lq_stream stream) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!amps || !out_dev) return fail(LQ_ERR_INVALID_ARG, "NULL device pointer");
+  st = check_terms(n, terms, nt);
+  if (st) return st;
+  if (!workspace || ws_bytes < lq_expval_workspace_size(n, nt))
+    return fail(LQ_ERR_OOM, "workspace too small: %zu < %zu", ws_bytes,
+                lq_expval_workspace_size(n, nt));
+  cudaStream_t s = (cudaStream_t)stream;
+  double* partial = (double*)((char*)workspace + align256(sizeof(double)));
+  return expval_states((const double2*)amps, 0, 1, n, terms, nt, partial, out_dev, s);
+}
+
+lq_status lq_expval_pauli_sum(const void* amps, int n, const lq_pauli_term* terms, int nt,
+                              double* out, void* workspace, size_t ws_bytes,
+                              lq_stream stream) {
+  if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
+  if (!workspace) return fail(LQ_ERR_OOM, "workspace is NULL");
+  double* d_out = (double*)workspace;
+  lq_status st = lq_expval_pauli_sum_async(amps, n, terms, nt, d_out, workspace, ws_bytes,
+                                           stream);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  LQ_CUDA(cudaMemcpyAsync(out, d_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  LQ_CUDA(cudaStreamSynchronize(s));
+  return LQ_OK;
+}
+
+lq_status lq_apply_pauli_sum(void* out, const void* in, int n, const lq_pauli_term* terms,
+                             int nt, lq_stream stream) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!out || !in) return fail(LQ_ERR_INVALID_ARG, "NULL device pointer");
+  if (out == in) return fail(LQ_ERR_INVALID_ARG, "out must differ from in");
+  st = check_terms(n, terms, nt);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nt == 0) {
+    LQ_CUDA(cudaMemsetAsync(out, 0, sizeof(double2) << n, s));
+    return LQ_OK;
+  }
+  int nch = exp_chunk_count(terms, nt);
+  std::vector<ExpParams> ch((std::size_t)nch);
+  int got = build_exp_chunks(n, terms, nt, ch.data(), nch);
+  if (got < 0) return fail(LQ_ERR_INVALID_ARG, "internal: term chunking");
+  for (int c = 0; c < got; c++)
+    LQ_CUDA(launch_apply_pauli_sum(ch[c], (const double2*)in, (double2*)out, c > 0, s));
+  return LQ_OK;
+}
+
+}  // extern "C"

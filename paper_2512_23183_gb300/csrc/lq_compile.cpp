@@ -1,0 +1,430 @@
+// lq_compile.cpp -- host side of lq_apply_circuit and friends: validation,
+// lowering of gates into tile ops, and greedy packing of ops into
+// shared-memory tile passes.
+//
+// Lowering follows the gate definitions of the paper (rotations
+// exp(-i theta sigma/2), Sec. III-A; CNOT and Toffoli as the bit-mask swaps of
+// Alg. 1 and Alg. 4; CP as diag(1,1,1,e^{i theta}), Alg. 3) with qubit q at bit
+// n-1-q of the amplitude index (MSB-first).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lq_coefs.h"
+#include "lq_internal.h"
+
+namespace lq {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+lq_status fail(lq_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+const char* last_error() { return g_err; }
+void clear_error() { g_err[0] = 0; }
+
+static inline int popc64(uint64_t v) { return __builtin_popcountll(v); }
+
+// ------------------------------------------------------------- validation
+
+int gate_arity(int kind) {
+  switch (kind) {
+    case LQ_H: case LQ_X: case LQ_Y: case LQ_Z: case LQ_S: case LQ_SDG: case LQ_T:
+    case LQ_TDG: case LQ_RX: case LQ_RY: case LQ_RZ: case LQ_P: case LQ_U1:
+      return 1;
+    case LQ_CNOT: case LQ_CY: case LQ_CZ: case LQ_CP: case LQ_SWAP: case LQ_CRX:
+    case LQ_CRY: case LQ_CRZ: case LQ_RXX: case LQ_RYY: case LQ_RZZ: case LQ_U2:
+      return 2;
+    case LQ_CCX:
+      return 3;
+    default:
+      return 0;
+  }
+}
+
+bool gate_takes_angle(int kind) {
+  switch (kind) {
+    case LQ_RX: case LQ_RY: case LQ_RZ: case LQ_P: case LQ_CP: case LQ_CRX: case LQ_CRY:
+    case LQ_CRZ: case LQ_RXX: case LQ_RYY: case LQ_RZZ:
+      return true;
+    default:
+      return false;
+  }
+}
+
+lq_status check_n(int n) {
+  if (n < 1 || n > 34) return fail(LQ_ERR_INVALID_ARG, "n=%d outside [1, 34]", n);
+  return LQ_OK;
+}
+
+lq_status check_gates(int n, const lq_gate* gates, int ng, const double* params, int np) {
+  if (ng < 0 || np < 0) return fail(LQ_ERR_INVALID_ARG, "negative gate or parameter count");
+  if (ng > 0 && !gates) return fail(LQ_ERR_INVALID_ARG, "gates is NULL");
+  if (np > 0 && !params) return fail(LQ_ERR_INVALID_ARG, "params is NULL");
+  for (int i = 0; i < np; i++)
+    if (!std::isfinite(params[i]))
+      return fail(LQ_ERR_NONFINITE, "params[%d] is not finite", i);
+  for (int g = 0; g < ng; g++) {
+    const lq_gate& G = gates[g];
+    int k = gate_arity(G.kind);
+    if (k == 0) return fail(LQ_ERR_INVALID_ARG, "gate %d: unknown kind %d", g, G.kind);
+    for (int j = 0; j < k; j++) {
+      if (G.qubits[j] < 0 || G.qubits[j] >= n)
+        return fail(LQ_ERR_INVALID_ARG, "gate %d: qubit %d outside [0, %d)", g, G.qubits[j], n);
+      for (int l = 0; l < j; l++)
+        if (G.qubits[l] == G.qubits[j])
+          return fail(LQ_ERR_INVALID_ARG, "gate %d: qubit %d repeated", g, G.qubits[j]);
+    }
+    if (G.param >= 0) {
+      if (!gate_takes_angle(G.kind))
+        return fail(LQ_ERR_INVALID_ARG, "gate %d: kind %d takes no parameter", g, G.kind);
+      if (G.param >= np)
+        return fail(LQ_ERR_INVALID_ARG, "gate %d: parameter index %d >= np=%d", g, G.param, np);
+    } else if (G.param < -1) {
+      return fail(LQ_ERR_INVALID_ARG, "gate %d: parameter index %d", g, G.param);
+    }
+    if (!std::isfinite(G.angle)) return fail(LQ_ERR_NONFINITE, "gate %d: angle not finite", g);
+    int nm = G.kind == LQ_U1 ? 8 : G.kind == LQ_U2 ? 32 : 0;
+    for (int i = 0; i < nm; i++)
+      if (!std::isfinite(G.mat[i])) return fail(LQ_ERR_NONFINITE, "gate %d: matrix not finite", g);
+  }
+  return LQ_OK;
+}
+
+lq_status check_terms(int n, const lq_pauli_term* terms, int nt) {
+  if (nt < 0) return fail(LQ_ERR_INVALID_ARG, "negative term count");
+  if (nt > 0 && !terms) return fail(LQ_ERR_INVALID_ARG, "terms is NULL");
+  uint64_t lim = n >= 64 ? ~0ull : ((1ull << n) - 1);
+  for (int t = 0; t < nt; t++) {
+    if (!std::isfinite(terms[t].coeff))
+      return fail(LQ_ERR_NONFINITE, "term %d: coefficient not finite", t);
+    if ((terms[t].xmask | terms[t].zmask) & ~lim)
+      return fail(LQ_ERR_INVALID_ARG, "term %d: mask has bits >= n=%d", t, n);
+  }
+  return LQ_OK;
+}
+
+// ---------------------------------------------------------------- lowering
+
+uint64_t LOp::mix() const {
+  switch (type) {
+    case OP_PAULI: case OP_GRAD: return x;
+    case OP_H: case OP_PAIR_GEN: return 1ull << g0;
+    case OP_QUAD_GEN: case OP_SWAP: return (1ull << g0) | (1ull << g1);
+    default: return 0;
+  }
+}
+
+uint64_t LOp::diag() const { return cm | z; }
+
+static LOp pauli_op(uint64_t x, uint64_t z, int ny, uint8_t pmode) {
+  LOp o;
+  o.type = OP_PAULI;
+  o.x = x;
+  o.z = z;
+  // w_i = (-i)^{rotations} i^{ny}: rotations carry the -i of c - i s P
+  int k0 = (pmode == PM_PERM) ? (ny & 3) : ((3 + ny) & 3);
+  o.mode = (uint8_t)(pmode | (k0 << 2));
+  return o;
+}
+
+static LOp diag_op(uint8_t type, uint64_t cm, uint64_t cv, double a, double b) {
+  LOp o;
+  o.type = type;
+  o.cm = cm;
+  o.cv = cv;
+  o.a = a;
+  o.b = b;
+  return o;
+}
+
+lq_status lower_gate(const lq_gate& g, int n, double theta, Lowered& L) {
+  L = Lowered();
+  int b[3] = {0, 0, 0};
+  int k = gate_arity(g.kind);
+  for (int j = 0; j < k; j++) b[j] = n - 1 - g.qubits[j];
+  const uint64_t m0 = 1ull << b[0], m1 = k > 1 ? 1ull << b[1] : 0, m2 = k > 2 ? 1ull << b[2] : 0;
+  const double R2 = 0.70710678118654752440;
+  AngleCoefs ac;
+  if (gate_takes_angle(g.kind)) angle_coefs(g.kind, theta, ac);
+  L.zr = ac.zr;
+  L.zi = ac.zi;
+  LOp& o = L.op[0];
+  L.nops = 1;
+  switch (g.kind) {
+    case LQ_H:
+      o.type = OP_H; o.g0 = b[0];
+      L.zr = R2; L.zi = 0;
+      break;
+    case LQ_X: o = pauli_op(m0, 0, 0, PM_PERM); break;
+    case LQ_Y: o = pauli_op(m0, m0, 1, PM_PERM); break;
+    case LQ_Z: o = diag_op(OP_SIGN, m0, m0, 0, 0); break;
+    case LQ_S: o = diag_op(OP_MULI, m0, m0, 0, 0); o.mode = 1; break;
+    case LQ_SDG: o = diag_op(OP_MULI, m0, m0, 0, 0); o.mode = 3; break;
+    case LQ_T: o = diag_op(OP_PHASE, m0, m0, R2, R2); break;
+    case LQ_TDG: o = diag_op(OP_PHASE, m0, m0, R2, -R2); break;
+    case LQ_RX: o = pauli_op(m0, 0, 0, ac.mode0); o.a = ac.a0; o.b = ac.b0; break;
+    case LQ_RY: o = pauli_op(m0, m0, 1, ac.mode0); o.a = ac.a0; o.b = ac.b0; break;
+    case LQ_RZ: case LQ_P: o = diag_op(OP_PHASE, m0, m0, ac.a0, ac.b0); break;
+    case LQ_U1:
+      o.type = OP_PAIR_GEN; o.g0 = b[0]; o.ncoef = 8;
+      for (int i = 0; i < 8; i++) o.coef[i] = g.mat[i];
+      break;
+    case LQ_CNOT: o = pauli_op(m1, 0, 0, PM_PERM); o.cm = m0; o.cv = m0; break;
+    case LQ_CY: o = pauli_op(m1, m1, 1, PM_PERM); o.cm = m0; o.cv = m0; break;
+    case LQ_CZ: o = diag_op(OP_SIGN, m0 | m1, m0 | m1, 0, 0); break;
+    case LQ_CP: o = diag_op(OP_PHASE, m0 | m1, m0 | m1, ac.a0, ac.b0); break;
+    case LQ_SWAP: o.type = OP_SWAP; o.g0 = b[0]; o.g1 = b[1]; break;
+    case LQ_CRX:
+      o = pauli_op(m1, 0, 0, PM_GEN); o.a = ac.a0; o.b = ac.b0; o.cm = m0; o.cv = m0;
+      break;
+    case LQ_CRY:
+      o = pauli_op(m1, m1, 1, PM_GEN); o.a = ac.a0; o.b = ac.b0; o.cm = m0; o.cv = m0;
+      break;
+    case LQ_CRZ:
+      o = diag_op(OP_PHASE, m0 | m1, m0, ac.a0, ac.b0);
+      L.op[1] = diag_op(OP_PHASE, m0 | m1, m0 | m1, ac.a1, ac.b1);
+      L.op[1].sub = 1;
+      L.nops = 2;
+      break;
+    case LQ_RXX: o = pauli_op(m0 | m1, 0, 0, ac.mode0); o.a = ac.a0; o.b = ac.b0; break;
+    case LQ_RYY:
+      o = pauli_op(m0 | m1, m0 | m1, 2, ac.mode0); o.a = ac.a0; o.b = ac.b0;
+      break;
+    case LQ_RZZ:
+      o = diag_op(OP_PARITY, 0, 0, ac.a0, ac.b0); o.z = m0 | m1;
+      break;
+    case LQ_CCX: o = pauli_op(m2, 0, 0, PM_PERM); o.cm = m0 | m1; o.cv = m0 | m1; break;
+    case LQ_U2:
+      o.type = OP_QUAD_GEN; o.g0 = b[0]; o.g1 = b[1]; o.ncoef = 32;
+      for (int i = 0; i < 32; i++) o.coef[i] = g.mat[i];
+      break;
+    default:
+      return fail(LQ_ERR_INVALID_ARG, "unknown gate kind %d", g.kind);
+  }
+  return LQ_OK;
+}
+
+// Magnitude window of the deferred scalar; outside it the magnitude is applied
+// by an explicit OP_SCALE so stored amplitudes stay far from overflow.
+static const double kScaleLo = 1e-100, kScaleHi = 1e100;
+
+lq_status lower_circuit(int n, const lq_gate* gates, int ng, const double* params, int np,
+                        LOp** ops_out, std::size_t* nops_out, double* zr_out, double* zi_out) {
+  lq_status st = check_gates(n, gates, ng, params, np);
+  if (st) return st;
+  std::vector<LOp> ops;
+  ops.reserve((std::size_t)ng + 8);
+  double zr = 1, zi = 0;
+  for (int g = 0; g < ng; g++) {
+    double th = gates[g].angle + (gates[g].param >= 0 ? params[gates[g].param] : 0.0);
+    Lowered L;
+    st = lower_gate(gates[g], n, th, L);
+    if (st) return st;
+    for (int j = 0; j < L.nops; j++) {
+      L.op[j].gate = g;
+      ops.push_back(L.op[j]);
+    }
+    double nr = zr * L.zr - zi * L.zi, ni = zr * L.zi + zi * L.zr;
+    zr = nr;
+    zi = ni;
+    double mag = std::hypot(zr, zi);
+    if (mag < kScaleLo || mag > kScaleHi) {
+      LOp s;
+      s.type = OP_SCALE;
+      s.mode = 1;
+      s.a = mag;
+      ops.push_back(s);
+      zr /= mag;
+      zi /= mag;
+    }
+  }
+  LOp* out = new LOp[ops.size() > 0 ? ops.size() : 1];
+  for (std::size_t i = 0; i < ops.size(); i++) out[i] = ops[i];
+  *ops_out = out;
+  *nops_out = ops.size();
+  *zr_out = zr;
+  *zi_out = zi;
+  return LQ_OK;
+}
+
+// ------------------------------------------------------------ cost model
+
+double op_flops(const LOp& o, int n) {
+  const double N = std::ldexp(1.0, n);
+  const double frac = std::ldexp(1.0, -popc64(o.cm));  // amplitudes meeting the condition
+  switch (o.type) {
+    case OP_PAULI:
+      switch (o.mode & 3) {
+        case PM_TAN: case PM_COT: return 4.0 * N * frac;   // 2 FMA per amplitude
+        case PM_GEN: return 6.0 * N * frac;                // MUL + FMA per component
+        default: return 0.0;                               // permutation
+      }
+    case OP_H: return 2.0 * N * frac;                      // 2 adds per amplitude
+    case OP_PAIR_GEN: return 14.0 * N * frac;              // 1 MUL + 3 FMA per component
+    case OP_QUAD_GEN: return 32.0 * N * frac;              // 8 FMA per component
+    case OP_PHASE: return 6.0 * N * frac;                  // complex multiply
+    case OP_PARITY: return 6.0 * N * 0.5 * frac;
+    case OP_SCALE: return ((o.mode & 1) ? 2.0 : 6.0) * N;
+    case OP_GRAD: return 4.0 * N;
+    default: return 0.0;                                   // sign flips, i^k, swaps
+  }
+}
+
+// -------------------------------------------------------------- scheduling
+
+Schedule::~Schedule() {
+  delete[] passes;
+  delete[] op_src;
+}
+
+static uint32_t to_local(uint64_t mask, const int* pos) {
+  uint32_t r = 0;
+  while (mask) {
+    int b = __builtin_ctzll(mask);
+    mask &= mask - 1;
+    r |= 1u << pos[b];
+  }
+  return r;
+}
+
+static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef_at) {
+  std::memset(&d, 0, sizeof d);
+  d.type = s.type;
+  d.mode = s.mode;
+  d.b0 = s.g0 >= 0 ? (uint8_t)pos[s.g0] : 0;
+  d.b1 = s.g1 >= 0 ? (uint8_t)pos[s.g1] : (uint8_t)s.sub;
+  if (s.type == OP_GRAD)
+    d.cidx = (uint32_t)s.slot;
+  else if (s.type == OP_PAIR_GEN || s.type == OP_QUAD_GEN)
+    d.cidx = (uint32_t)coef_at;
+  else
+    d.cidx = (uint32_t)s.gate;
+  d.cm_loc = to_local(s.cm & tile, pos);
+  d.cv_loc = to_local(s.cv & tile, pos);
+  d.cm_glob = s.cm & ~tile;
+  d.cv_glob = s.cv & ~tile;
+  d.x_loc = to_local(s.x, pos);
+  d.z_loc = to_local(s.z & tile, pos);
+  d.z_glob = s.z & ~tile;
+  d.a = s.a;
+  d.b = s.b;
+}
+
+lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, double zi,
+                       const ScheduleOptions& opt, Schedule& out) {
+  const int k = opt.k < n ? opt.k : n;
+  const int m = opt.m < k ? opt.m : k;
+  if (k > MAX_TILE_BITS || k < 1) return fail(LQ_ERR_INVALID_ARG, "tile bits %d", k);
+  const uint64_t low = (m >= 64) ? ~0ull : ((1ull << m) - 1);
+  const bool need_scale = opt.force_scale || !(zr == 1.0 && zi == 0.0);
+
+  struct Built {
+    uint64_t tile;
+    std::vector<int> idx;
+  };
+  std::vector<Built> passes;
+  std::vector<int> pending(nops);
+  for (std::size_t i = 0; i < nops; i++) pending[i] = (int)i;
+
+  while (!pending.empty()) {
+    Built B;
+    B.tile = low;
+    int coefs = 0;
+    std::vector<int> skipped;
+    uint64_t blocked_mix = 0, blocked_all = 0;
+    for (int idx : pending) {
+      const LOp& o = ops[idx];
+      uint64_t mx = o.mix(), dg = o.diag();
+      bool commutes = !(mx & blocked_all) && !(dg & blocked_mix);
+      bool room = (int)B.idx.size() < MAX_OPS - 1 && coefs + o.ncoef <= MAX_COEF;
+      if (commutes && room) {
+        uint64_t t = B.tile | mx;
+        if (popc64(t) <= k) {
+          B.tile = t;
+          B.idx.push_back(idx);
+          coefs += o.ncoef;
+          continue;
+        }
+      }
+      skipped.push_back(idx);
+      blocked_mix |= mx;
+      blocked_all |= mx | dg;
+    }
+    if (B.idx.empty()) return fail(LQ_ERR_INVALID_ARG, "internal: op cannot be scheduled");
+    passes.push_back(std::move(B));
+    pending.swap(skipped);
+  }
+  if (passes.empty() && need_scale) passes.push_back(Built{low, {}});
+
+  out.n = n;
+  out.npasses = (int)passes.size();
+  delete[] out.passes;
+  delete[] out.op_src;
+  out.passes = new PassParams[passes.size() > 0 ? passes.size() : 1];
+  out.op_src = new int[(passes.size() > 0 ? passes.size() : 1) * MAX_OPS];
+  for (std::size_t p = 0; p < passes.size(); p++) {
+    Built& B = passes[p];
+    // fill the tile up to k bits with the lowest unused bits (larger
+    // contiguous loads, fewer tiles)
+    for (int bit = 0; bit < n && popc64(B.tile) < k; bit++) B.tile |= 1ull << bit;
+    PassParams& P = out.passes[p];
+    std::memset(&P.h, 0, sizeof P.h);
+    P.h.n = n;
+    P.h.k = k;
+    P.h.m = m;
+    int pos[64];
+    for (int i = 0; i < 64; i++) pos[i] = -1;
+    int j = 0, o = 0;
+    for (int bit = 0; bit < n; bit++) {
+      if (B.tile >> bit & 1) {
+        P.h.tbits[j] = (int8_t)bit;
+        pos[bit] = j++;
+      } else {
+        P.h.obits[o++] = (int8_t)bit;
+      }
+    }
+    // contiguous low run: tile bits 0..m'-1 where every lower bit is in
+    int mm = 0;
+    while (mm < k && P.h.tbits[mm] == mm) mm++;
+    P.h.m = mm;
+    P.h.nobits = o;
+    P.h.ntiles = 1ull << (n - k);
+    int coef_at = 0, cnt = 0;
+    for (int idx : B.idx) {
+      fill_op(P.ops[cnt], ops[idx], B.tile, pos, coef_at);
+      for (int c = 0; c < ops[idx].ncoef; c++) P.coef[coef_at + c] = ops[idx].coef[c];
+      coef_at += ops[idx].ncoef;
+      out.op_src[p * MAX_OPS + cnt] = idx;
+      cnt++;
+    }
+    if (p + 1 == passes.size() && need_scale) {
+      LOp s;
+      s.type = OP_SCALE;
+      s.mode = (uint8_t)((zi == 0.0 ? 1 : 0) | 2);
+      s.a = zr;
+      s.b = zi;
+      fill_op(P.ops[cnt], s, B.tile, pos, 0);
+      out.op_src[p * MAX_OPS + cnt] = -1;
+      cnt++;
+    }
+    P.h.nops = cnt;
+  }
+  return LQ_OK;
+}
+
+}  // namespace lq

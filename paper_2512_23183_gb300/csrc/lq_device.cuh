@@ -1,0 +1,212 @@
+// lq_device.cuh -- device helpers shared by the lq kernels: complex
+// arithmetic in the forms the tile ops use, sign-bit manipulation without
+// FP64 instructions, bit deposit/insert, and the tile-op interpreter.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lq_internal.h"
+
+namespace lq {
+
+// Flip the sign of a double when `flip` is 0x80000000 (integer pipe only).
+__device__ __forceinline__ double xsign(double x, uint32_t flip) {
+  return __hiloint2double(__double2hiint(x) ^ (int)flip, __double2loint(x));
+}
+
+// v * i^k (k mod 4): register moves and sign flips, no FP64 instruction.
+__device__ __forceinline__ double2 mul_ipow(double2 v, int k) {
+  double re = (k & 1) ? v.y : v.x;
+  double im = (k & 1) ? v.x : v.y;
+  uint32_t sre = (uint32_t)((k + 1) & 2) << 30;
+  uint32_t sim = (uint32_t)(k & 2) << 30;
+  return make_double2(xsign(re, sre), xsign(im, sim));
+}
+
+__device__ __forceinline__ double2 cmul(double2 v, double wr, double wi) {
+  return make_double2(fma(v.x, wr, -v.y * wi), fma(v.x, wi, v.y * wr));
+}
+
+// Insert a zero bit at position b of j.
+__device__ __forceinline__ uint32_t insert0(uint32_t j, int b) {
+  uint32_t lo = j & ((1u << b) - 1u);
+  return ((j ^ lo) << 1) | lo;
+}
+__device__ __forceinline__ uint64_t insert0_64(uint64_t j, int b) {
+  uint64_t lo = j & ((1ull << b) - 1ull);
+  return ((j ^ lo) << 1) | lo;
+}
+
+// Scatter the low bits of v onto the bit positions pos[0..cnt).
+__device__ __forceinline__ uint64_t deposit(uint64_t v, const int8_t* pos, int cnt) {
+  uint64_t r = 0;
+  for (int i = 0; i < cnt; i++) r |= ((v >> i) & 1ull) << pos[i];
+  return r;
+}
+
+// Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
+// are `base`.  All threads of the block call it; the caller synchronises.
+template <int BLOCK>
+__device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, const Op& op,
+                                         const double* __restrict__ coef, uint64_t base) {
+  const uint32_t tid = threadIdx.x;
+  if ((base & op.cm_glob) != op.cv_glob) return;  // CTA-level condition
+  const int zs = __popcll(base & op.z_glob) & 1;
+  const uint32_t cm = op.cm_loc, cv = op.cv_loc;
+  switch (op.type) {
+    case OP_PAULI: {
+      const uint32_t x = op.x_loc, z = op.z_loc;
+      const int h = 31 - __clz(x);
+      const int k0 = op.mode >> 2, pm = op.mode & 3;
+      const double a = op.a, b = op.b;
+      for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
+        uint32_t s0 = insert0(j, h);
+        if ((s0 & cm) != cv) continue;
+        uint32_t s1 = s0 ^ x;
+        double2 A = sm[s0], B = sm[s1];
+        int kA = (k0 + 2 * ((__popc(s1 & z) + zs) & 1)) & 3;
+        int kB = (k0 + 2 * ((__popc(s0 & z) + zs) & 1)) & 3;
+        double2 Bw = mul_ipow(B, kA), Aw = mul_ipow(A, kB);
+        double2 o0, o1;
+        if (pm == PM_TAN) {
+          o0 = make_double2(fma(a, Bw.x, A.x), fma(a, Bw.y, A.y));
+          o1 = make_double2(fma(a, Aw.x, B.x), fma(a, Aw.y, B.y));
+        } else if (pm == PM_COT) {
+          o0 = make_double2(fma(a, A.x, Bw.x), fma(a, A.y, Bw.y));
+          o1 = make_double2(fma(a, B.x, Aw.x), fma(a, B.y, Aw.y));
+        } else if (pm == PM_GEN) {
+          o0 = make_double2(fma(b, Bw.x, a * A.x), fma(b, Bw.y, a * A.y));
+          o1 = make_double2(fma(b, Aw.x, a * B.x), fma(b, Aw.y, a * B.y));
+        } else {
+          o0 = Bw;
+          o1 = Aw;
+        }
+        sm[s0] = o0;
+        sm[s1] = o1;
+      }
+      break;
+    }
+    case OP_H: {
+      const int bb = op.b0;
+      for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
+        uint32_t s0 = insert0(j, bb);
+        if ((s0 & cm) != cv) continue;
+        uint32_t s1 = s0 | (1u << bb);
+        double2 A = sm[s0], B = sm[s1];
+        sm[s0] = make_double2(A.x + B.x, A.y + B.y);
+        sm[s1] = make_double2(A.x - B.x, A.y - B.y);
+      }
+      break;
+    }
+    case OP_PAIR_GEN: {
+      const int bb = op.b0;
+      const double* M = coef + op.cidx;
+      const double m00r = M[0], m00i = M[1], m01r = M[2], m01i = M[3];
+      const double m10r = M[4], m10i = M[5], m11r = M[6], m11i = M[7];
+      for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
+        uint32_t s0 = insert0(j, bb);
+        if ((s0 & cm) != cv) continue;
+        uint32_t s1 = s0 | (1u << bb);
+        double2 A = sm[s0], B = sm[s1];
+        double2 o0, o1;
+        o0.x = fma(m00r, A.x, fma(-m00i, A.y, fma(m01r, B.x, -m01i * B.y)));
+        o0.y = fma(m00r, A.y, fma(m00i, A.x, fma(m01r, B.y, m01i * B.x)));
+        o1.x = fma(m10r, A.x, fma(-m10i, A.y, fma(m11r, B.x, -m11i * B.y)));
+        o1.y = fma(m10r, A.y, fma(m10i, A.x, fma(m11r, B.y, m11i * B.x)));
+        sm[s0] = o0;
+        sm[s1] = o1;
+      }
+      break;
+    }
+    case OP_QUAD_GEN: {
+      const int hb = op.b0, lb = op.b1;
+      const int lo = hb < lb ? hb : lb, hi = hb < lb ? lb : hb;
+      const double* M = coef + op.cidx;
+      for (uint32_t j = tid; j < (T >> 2); j += BLOCK) {
+        uint32_t s = insert0(insert0(j, lo), hi);
+        if ((s & cm) != cv) continue;
+        uint32_t idx[4] = {s, s | (1u << lb), s | (1u << hb), s | (1u << hb) | (1u << lb)};
+        double2 v[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) v[c] = sm[idx[c]];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          double re = 0, im = 0;
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            double mr = M[2 * (4 * r + c)], mi = M[2 * (4 * r + c) + 1];
+            re = fma(mr, v[c].x, fma(-mi, v[c].y, re));
+            im = fma(mr, v[c].y, fma(mi, v[c].x, im));
+          }
+          sm[idx[r]] = make_double2(re, im);
+        }
+      }
+      break;
+    }
+    case OP_SWAP: {
+      const int b0 = op.b0, b1 = op.b1;
+      const int lo = b0 < b1 ? b0 : b1, hi = b0 < b1 ? b1 : b0;
+      for (uint32_t j = tid; j < (T >> 2); j += BLOCK) {
+        uint32_t s = insert0(insert0(j, lo), hi);
+        if ((s & cm) != cv) continue;
+        uint32_t sa = s | (1u << b0), sb = s | (1u << b1);
+        double2 A = sm[sa];
+        sm[sa] = sm[sb];
+        sm[sb] = A;
+      }
+      break;
+    }
+    case OP_PHASE: {
+      const double wr = op.a, wi = op.b;
+      for (uint32_t s = tid; s < T; s += BLOCK) {
+        if ((s & cm) != cv) continue;
+        sm[s] = cmul(sm[s], wr, wi);
+      }
+      break;
+    }
+    case OP_SIGN: {
+      for (uint32_t s = tid; s < T; s += BLOCK) {
+        if ((s & cm) != cv) continue;
+        double2 v = sm[s];
+        sm[s] = make_double2(xsign(v.x, 0x80000000u), xsign(v.y, 0x80000000u));
+      }
+      break;
+    }
+    case OP_MULI: {
+      const int kk = op.mode & 3;
+      for (uint32_t s = tid; s < T; s += BLOCK) {
+        if ((s & cm) != cv) continue;
+        sm[s] = mul_ipow(sm[s], kk);
+      }
+      break;
+    }
+    case OP_PARITY: {
+      const uint32_t z = op.z_loc;
+      const double wr = op.a, wi = op.b;
+      for (uint32_t s = tid; s < T; s += BLOCK) {
+        if (((__popc(s & z) + zs) & 1) == 0) continue;
+        if ((s & cm) != cv) continue;
+        sm[s] = cmul(sm[s], wr, wi);
+      }
+      break;
+    }
+    case OP_SCALE: {
+      const double wr = op.a, wi = op.b;
+      if (op.mode & 1) {
+        for (uint32_t s = tid; s < T; s += BLOCK) {
+          double2 v = sm[s];
+          sm[s] = make_double2(v.x * wr, v.y * wr);
+        }
+      } else {
+        for (uint32_t s = tid; s < T; s += BLOCK) sm[s] = cmul(sm[s], wr, wi);
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+}  // namespace lq

@@ -1,0 +1,196 @@
+// lq_internal.h -- internal data structures of the lq library: the lowered
+// "op" encoding of gates executed by the tile-pass kernels, the pass
+// descriptors, and the host-side compiler interface.
+//
+// A gate of the circuit (Sec. II-A) is lowered into ops that work on a
+// shared-memory tile of 2^k amplitudes whose index bits are a chosen set of
+// k state-index bits ("tile bits"; the lowest m are always the contiguous low
+// bits so tile loads are coalesced).  Every other bit of the index is fixed
+// for the tile ("CTA bits").  Mixing ops (pairs/quads of amplitudes) need
+// their mixing bits inside the tile; diagonal ops and control conditions may
+// use any bit: for CTA bits they reduce to per-tile constants.
+//
+// FP64 economy.  On GB300 an FP64 instruction costs ~1/3 of a 32-byte HBM pass
+// per amplitude (1.19 TFLOP/s FP64 against 6.8 TB/s), so ops are encoded in
+// the forms with the fewest FP64 instructions:
+//   * Pauli rotations exp(-i theta P / 2) in tangent form
+//       out_i = c (psi_i + t w_i psi_{i^x}),  t = tan(theta/2)
+//     (or cotangent form when |t| > 1) with the real factor c deferred into a
+//     global scalar: 2 FP64 FMAs per amplitude;
+//   * H as (a + b, a - b) with 1/sqrt2 deferred: 2 FP64 adds per amplitude;
+//   * permutations, signs and multiplications by +-i (X, Y, Z, S, CNOT, CY,
+//     CZ, SWAP, CCX) move or flip sign bits only: no FP64 instruction;
+//   * diagonal phases (RZ, P, CP, T, RZZ) multiply only the amplitudes they
+//     change, with global phases deferred.
+// The deferred scalar is applied once, by an OP_SCALE at the end.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/lq.h"
+
+#if defined(__CUDACC__)
+#define LQ_HD __host__ __device__
+#else
+#define LQ_HD
+#endif
+
+namespace lq {
+
+// ------------------------------------------------------------------ ops
+
+enum OpType : uint8_t {
+  OP_PAULI = 0,   // out_i = alpha psi_i + beta w_i psi_{i^x}  (see PauliMode)
+  OP_H,           // (a, b) -> (a + b, a - b) on tile bit b0
+  OP_PAIR_GEN,    // 2x2 complex matrix on tile bit b0 (coef pool)
+  OP_QUAD_GEN,    // 4x4 complex matrix on tile bits b0 (high), b1 (low)
+  OP_SWAP,        // exchange tile bits b0 and b1
+  OP_PHASE,       // multiply matching amplitudes by (a + i b)
+  OP_SIGN,        // negate matching amplitudes
+  OP_MULI,        // multiply matching amplitudes by i^mode
+  OP_PARITY,      // multiply amplitudes with odd popcount(idx & z) by (a + i b)
+  OP_SCALE,       // multiply every amplitude by (a + i b) (mode 1: b == 0)
+  OP_GRAD,        // adjoint: accumulate Im <lam| G |psi> into slot cidx
+  OP_TYPE_COUNT
+};
+
+// OP_PAULI sub-modes (low 2 bits of Op::mode; bits 2-3 hold k0, the power of
+// i of the fixed phase, w_i = i^k0 (-1)^popcount((i ^ x) & z)).
+enum PauliMode : uint8_t {
+  PM_TAN = 0,   // alpha = 1, beta = a     (deferred factor cos)
+  PM_COT = 1,   // alpha = a, beta = 1     (deferred factor sin)
+  PM_GEN = 2,   // alpha = a, beta = b     (controlled rotations)
+  PM_PERM = 3   // alpha = 0, beta = 1     (X, Y, CNOT, CY, CCX)
+};
+
+// A condition is "(idx & cm) == cv"; split into tile-local bits (cm_loc,
+// cv_loc: positions are tile-local bit numbers) and CTA bits (cm_glob,
+// cv_glob: global bit positions).
+struct Op {
+  uint8_t type;
+  uint8_t mode;       // Pauli mode | k0 << 2; OP_MULI: power of i; OP_SCALE:
+                      // bit 0 real factor, bit 1 final scale of the circuit
+  uint8_t b0, b1;     // tile-local bit positions (b1 of a diagonal or Pauli
+                      // op: index of the op among its gate's ops)
+  uint32_t cidx;      // coef-pool index (PAIR_GEN/QUAD_GEN), grad slot
+                      // (OP_GRAD), else source gate index
+  uint32_t cm_loc, cv_loc;
+  uint32_t x_loc, z_loc;
+  uint64_t cm_glob, cv_glob;
+  uint64_t z_glob;
+  double a, b;
+};
+static_assert(sizeof(Op) == 64, "Op must stay 64 bytes");
+
+constexpr int MAX_TILE_BITS = 13;   // 2^13 amplitudes = 128 KiB of shared memory
+constexpr int MAX_OPS = 384;        // per pass (kernel-parameter budget)
+constexpr int MAX_COEF = 512;       // doubles per pass coefficient pool
+
+// Everything a tile pass needs; passed by value as a __grid_constant__
+// kernel parameter (< 32 KiB), so a pass needs no device allocation.
+struct PassHeader {
+  int32_t n, k, m, nops;
+  int32_t nobits;
+  int32_t flags;          // PF_* below
+  uint64_t ntiles;        // 2^(n-k)
+  int8_t tbits[16];       // tile-local bit j -> global bit position
+  int8_t obits[48];       // CTA bits (global positions), ascending
+};
+enum PassFlags : int32_t {
+  PF_INIT_ZERO = 1,       // do not load: start from |0...0> (whole-state tile)
+  PF_NO_STORE = 2,        // do not store the tile back
+};
+
+struct PassParams {
+  PassHeader h;
+  Op ops[MAX_OPS];
+  double coef[MAX_COEF];
+};
+
+// ----------------------------------------------------- host-side compiler
+
+// A lowered op with global bit positions, before tile assignment.
+struct LOp {
+  uint8_t type = 0, mode = 0;
+  int g0 = -1, g1 = -1;          // global mixing bits
+  uint64_t cm = 0, cv = 0;       // condition (global bits)
+  uint64_t x = 0, z = 0;         // Pauli masks (global bits)
+  double a = 0, b = 0;
+  int ncoef = 0;
+  double coef[32];
+  int gate = -1;                 // source gate index (-1: synthetic)
+  int sub = 0;                   // index of this op among its gate's ops
+  int slot = -1;                 // gradient slot (OP_GRAD)
+  uint64_t mix() const;          // bits that must lie inside the tile
+  uint64_t diag() const;         // bits only read (conditions, phases)
+};
+
+// Result of lowering one gate at a given angle.
+struct Lowered {
+  int nops = 0;
+  LOp op[2];
+  double zr = 1, zi = 0;         // deferred scalar factor
+};
+
+// Lower one gate (kind, global bits derived from qubits) at angle theta.
+// Returns LQ_OK or an error status (message set).
+lq_status lower_gate(const lq_gate& g, int n, double theta, Lowered& out);
+
+// Pass schedule: one PassParams per tile pass, in execution order.
+struct ScheduleOptions {
+  int k = 10;                // tile bits
+  int m = 5;                 // contiguous low bits always in the tile
+  bool force_scale = false;  // always end with a (final) OP_SCALE
+};
+
+// Per-state replacement of one gate's coefficients (shifted circuits of the
+// parameter-shift rule).  The final OP_SCALE is multiplied by (zr, zi), the
+// ratio of the shifted to the unshifted deferred factor.
+struct Patch {
+  int32_t gate;
+  uint8_t mode0, mode1, pad0, pad1;
+  double a0, b0, a1, b1;
+  double zr, zi;
+};
+
+struct Schedule {
+  int n = 0;
+  int npasses = 0;
+  PassParams* passes = nullptr;   // host array (npasses)
+  int* op_src = nullptr;          // npasses * MAX_OPS: index of the source LOp
+  Schedule() = default;
+  Schedule(const Schedule&) = delete;
+  Schedule& operator=(const Schedule&) = delete;
+  ~Schedule();
+};
+
+// Greedily pack `ops` (in order) into tile passes of opt.k bits; an op may
+// move ahead of ops it commutes with.  The deferred scalar (zr, zi) is
+// appended as an OP_SCALE to the last pass (no pass is added for an empty
+// circuit with a unit scalar).
+lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, double zi,
+                       const ScheduleOptions& opt, Schedule& out);
+
+// Validate and lower a whole circuit at the given parameters.  The caller
+// owns *ops_out (delete[]).  (*zr, *zi) is the product of deferred factors.
+lq_status lower_circuit(int n, const lq_gate* gates, int ng, const double* params, int np,
+                        LOp** ops_out, std::size_t* nops_out, double* zr, double* zi);
+
+// FP64 flops one op executes on a 2^n state (FMA = 2), in the op forms of the
+// tile kernels.
+double op_flops(const LOp& o, int n);
+
+// Validation helpers.
+lq_status check_n(int n);
+lq_status check_gates(int n, const lq_gate* gates, int ng, const double* params, int np);
+lq_status check_terms(int n, const lq_pauli_term* terms, int nt);
+bool gate_takes_angle(int kind);
+int gate_arity(int kind);
+
+// ------------------------------------------------------------ utilities
+
+void set_error(const char* fmt, ...);
+lq_status fail(lq_status st, const char* fmt, ...);
+
+}  // namespace lq

@@ -1,0 +1,251 @@
+// lq_kernels.cu -- state initialisation, the shared-memory tile-pass kernel
+// that executes lowered gate ops (Sec. IV-A direct state-vector updates, Alg. 1,
+// Alg. 4), and the Pauli-sum kernels (<H>, H psi; Sec. VI-A, Sec. VII-A-2).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lq_device.cuh"
+#include "lq_kernels.h"
+
+namespace lq {
+
+// ------------------------------------------------------------------ init
+
+__global__ void init_basis_kernel(double2* __restrict__ amps, uint64_t N, uint64_t basis) {
+  uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (; i < N; i += stride) amps[i] = make_double2(i == basis ? 1.0 : 0.0, 0.0);
+}
+
+cudaError_t launch_init_basis(double2* amps, int n, uint64_t basis, cudaStream_t s) {
+  uint64_t N = 1ull << n;
+  uint64_t blocks = (N + 255) / 256;
+  int grid = (int)(blocks < (uint64_t)sm_count() * 16 ? blocks : (uint64_t)sm_count() * 16);
+  init_basis_kernel<<<grid, 256, 0, s>>>(amps, N, basis);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- tile passes
+
+// One CTA processes tiles w = blockIdx.x, blockIdx.x + gridDim.x, ... of the
+// `nstates` states (stride `stride` amplitudes apart); a tile is the 2^k
+// amplitudes base | deposit(s, tbits), s < 2^k.  Tile loads and stores are
+// coalesced runs of 2^m contiguous amplitudes.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) pass_kernel(const __grid_constant__ PassParams P,
+                                                     double2* __restrict__ state,
+                                                     uint64_t stride, int nstates,
+                                                     const Patch* __restrict__ patches) {
+  extern __shared__ double2 sm[];
+  __shared__ uint64_t hioff[256];
+  const int k = P.h.k, m = P.h.m, nops = P.h.nops;
+  const uint32_t T = 1u << k;
+  const uint32_t lowmask = (1u << m) - 1u;
+  const int kh = k - m;
+  for (uint32_t j = threadIdx.x; j < (1u << kh); j += BLOCK)
+    hioff[j] = deposit(j, P.h.tbits + m, kh);
+  const uint64_t ntiles = P.h.ntiles;
+  const uint64_t total = ntiles * (uint64_t)nstates;
+  __syncthreads();
+  for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const uint64_t si = w / ntiles, t = w - si * ntiles;
+    double2* __restrict__ st = state + si * stride;
+    const uint64_t base = deposit(t, P.h.obits, P.h.nobits);
+    if (P.h.flags & PF_INIT_ZERO) {
+      for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+        sm[s] = make_double2((base == 0 && s == 0) ? 1.0 : 0.0, 0.0);
+    } else {
+      for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+        sm[s] = st[base | hioff[s >> m] | (s & lowmask)];
+    }
+    __syncthreads();
+    if (patches == nullptr) {
+      for (int o = 0; o < nops; o++) {
+        apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base);
+        __syncthreads();
+      }
+    } else {
+      // shifted circuit: replace the coefficients of the patched gate's ops
+      // and multiply the final scale by the ratio of deferred factors
+      const Patch pt = patches[si];
+      for (int o = 0; o < nops; o++) {
+        Op op = P.ops[o];
+        if ((int)op.cidx == pt.gate &&
+            (op.type == OP_PAULI || op.type == OP_PHASE || op.type == OP_PARITY)) {
+          if (op.b1 == 0) {
+            op.a = pt.a0;
+            op.b = pt.b0;
+            if (op.type == OP_PAULI) op.mode = (uint8_t)((op.mode & ~3) | pt.mode0);
+          } else {
+            op.a = pt.a1;
+            op.b = pt.b1;
+          }
+        } else if (op.type == OP_SCALE && (op.mode & 2)) {
+          const double ar = op.a, ai = op.b;
+          op.a = ar * pt.zr - ai * pt.zi;
+          op.b = ar * pt.zi + ai * pt.zr;
+          op.mode &= ~1;
+        }
+        apply_op<BLOCK>(sm, T, op, P.coef, base);
+        __syncthreads();
+      }
+    }
+    if (!(P.h.flags & PF_NO_STORE)) {
+      for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+        st[base | hioff[s >> m] | (s & lowmask)] = sm[s];
+    }
+    __syncthreads();
+  }
+}
+
+static constexpr int kPassBlock = 256;
+
+cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, int nstates,
+                        cudaStream_t s, const Patch* patches) {
+  static bool configured = false;
+  size_t smem = sizeof(double2) << P.h.k;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<kPassBlock>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double2) << MAX_TILE_BITS));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  uint64_t total = P.h.ntiles * (uint64_t)nstates;
+  int per_sm = smem <= 16384 ? 8 : smem <= 32768 ? 6 : smem <= 65536 ? 3 : 1;
+  uint64_t cap = (uint64_t)sm_count() * per_sm;
+  int grid = (int)(total < cap ? total : cap);
+  pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, patches);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ Pauli sums
+
+// <H> over grouped terms.  Terms sharing an X mask form a group; a group with
+// x != 0 visits each unordered pair (i, i^x) once (i has the top bit of x
+// clear) and adds 2 c_t Re(conj(psi_i) <i|P_t|i^x> psi_{i^x}); the x == 0 group
+// adds c_t (-1)^popcount(i & z_t) |psi_i|^2.  <i|P|j> = i^k0 (-1)^popcount(j&z).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) expval_kernel(const __grid_constant__ ExpParams E,
+                                                       const double2* __restrict__ state,
+                                                       uint64_t stride,
+                                                       double* __restrict__ partial) {
+  const double2* __restrict__ st = state + blockIdx.y * stride;
+  const uint64_t N = 1ull << E.n;
+  const uint64_t nthreads = (uint64_t)gridDim.x * BLOCK;
+  const uint64_t t0 = blockIdx.x * (uint64_t)BLOCK + threadIdx.x;
+  double acc = 0.0;
+  for (int g = 0; g < E.ngroups; g++) {
+    const ExpGroup G = E.groups[g];
+    if (G.x == 0) {
+      for (uint64_t i = t0; i < N; i += nthreads) {
+        double2 v = st[i];
+        double p = fma(v.x, v.x, v.y * v.y);
+        for (int t = G.first; t < G.first + G.count; t++) {
+          uint32_t f = (uint32_t)(__popcll(i & E.terms[t].z) & 1) << 31;
+          acc = fma(xsign(E.terms[t].c, f), p, acc);
+        }
+      }
+    } else {
+      for (uint64_t j = t0; j < (N >> 1); j += nthreads) {
+        uint64_t i = insert0_64(j, G.h), l = i ^ G.x;
+        double2 a = st[i], b = st[l];
+        double vr = fma(a.x, b.x, a.y * b.y);
+        double vi = fma(a.x, b.y, -(a.y * b.x));
+        for (int t = G.first; t < G.first + G.count; t++) {
+          int kk = (E.terms[t].k0 + 2 * (__popcll(l & E.terms[t].z) & 1)) & 3;
+          // Re(i^kk v): vr, -vi, -vr, vi
+          double val = (kk & 1) ? vi : vr;
+          uint32_t f = (uint32_t)(((kk + 1) & 2) >> 1) << 31;
+          acc = fma(xsign(E.terms[t].c2, f), val, acc);
+        }
+      }
+    }
+  }
+  // block reduction in a fixed order
+  __shared__ double red[BLOCK / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int w = 0; w < BLOCK / 32; w++) s += red[w];
+    partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// Sum the partials of each state in a fixed order (deterministic), add into
+// out[state] when `accumulate`, else overwrite.
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int nparts,
+                                    int nstates, double* __restrict__ out, int accumulate) {
+  int sidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sidx >= nstates) return;
+  double s = 0;
+  for (int p = 0; p < nparts; p++) s += partial[(uint64_t)sidx * nparts + p];
+  out[sidx] = accumulate ? out[sidx] + s : s;
+}
+
+static constexpr int kExpBlock = 256;
+
+int expval_grid(int n) {
+  uint64_t pairs = 1ull << (n > 0 ? n - 1 : 0);
+  uint64_t blocks = (pairs + kExpBlock - 1) / kExpBlock;
+  uint64_t cap = (uint64_t)sm_count() * 4;
+  return (int)(blocks < cap ? blocks : cap);
+}
+
+cudaError_t launch_expval(const ExpParams& E, const double2* state, uint64_t stride,
+                          int nstates, double* partial, double* out, int accumulate,
+                          cudaStream_t s) {
+  int gx = expval_grid(E.n);
+  dim3 grid(gx, nstates);
+  expval_kernel<kExpBlock><<<grid, kExpBlock, 0, s>>>(E, state, stride, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sum_partials_kernel<<<(nstates + 127) / 128, 128, 0, s>>>(partial, gx, nstates, out,
+                                                             accumulate);
+  return cudaGetLastError();
+}
+
+// out_i (+)= sum_t c_t <i|P_t|i^x> psi_{i^x}, i.e. out (+)= H psi, one element per
+// thread iteration; `accumulate` adds into out (chunked term lists).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) apply_pauli_sum_kernel(
+    const __grid_constant__ ExpParams E, const double2* __restrict__ in,
+    double2* __restrict__ out, int accumulate) {
+  const uint64_t N = 1ull << E.n;
+  const uint64_t nthreads = (uint64_t)gridDim.x * BLOCK;
+  for (uint64_t i = blockIdx.x * (uint64_t)BLOCK + threadIdx.x; i < N; i += nthreads) {
+    double re = 0, im = 0;
+    if (accumulate) {
+      double2 o = out[i];
+      re = o.x;
+      im = o.y;
+    }
+    for (int g = 0; g < E.ngroups; g++) {
+      const ExpGroup G = E.groups[g];
+      const uint64_t l = i ^ G.x;
+      const double2 v = in[l];
+      for (int t = G.first; t < G.first + G.count; t++) {
+        int kk = (E.terms[t].k0 + 2 * (__popcll(l & E.terms[t].z) & 1)) & 3;
+        double2 w = mul_ipow(v, kk);
+        re = fma(E.terms[t].c, w.x, re);
+        im = fma(E.terms[t].c, w.y, im);
+      }
+    }
+    out[i] = make_double2(re, im);
+  }
+}
+
+cudaError_t launch_apply_pauli_sum(const ExpParams& E, const double2* in, double2* out,
+                                   int accumulate, cudaStream_t s) {
+  uint64_t N = 1ull << E.n;
+  uint64_t blocks = (N + 255) / 256;
+  uint64_t cap = (uint64_t)sm_count() * 8;
+  int grid = (int)(blocks < cap ? blocks : cap);
+  apply_pauli_sum_kernel<256><<<grid, 256, 0, s>>>(E, in, out, accumulate);
+  return cudaGetLastError();
+}
+
+}  // namespace lq

@@ -1,0 +1,69 @@
+// lq_kernels.h -- kernel launchers and kernel-parameter structs of the lq
+// library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lq_internal.h"
+
+namespace lq {
+
+// ------------------------------------------------------- Pauli-sum params
+
+struct ExpTerm {
+  double c;    // coefficient
+  double c2;   // 2 * coefficient (pair form of <H>)
+  uint64_t z;  // Z mask (global bits)
+  int32_t k0;  // number of Y factors mod 4
+  int32_t pad;
+};
+struct ExpGroup {
+  uint64_t x;   // common X mask
+  int32_t h;    // top bit of x (pair enumeration), 0 for x == 0
+  int32_t first, count;
+  int32_t pad;
+};
+constexpr int EXP_MAX_TERMS = 640;
+constexpr int EXP_MAX_GROUPS = 240;
+struct ExpParams {
+  int32_t n, ngroups;
+  ExpGroup groups[EXP_MAX_GROUPS];
+  ExpTerm terms[EXP_MAX_TERMS];
+};
+static_assert(sizeof(ExpParams) < 32000, "ExpParams exceeds the kernel parameter budget");
+
+// Group a term list by X mask into chunks that fit ExpParams.  Returns the
+// number of chunks written to `chunks` (caller-allocated with capacity
+// `max_chunks`), or -1 when max_chunks is too small.
+int build_exp_chunks(int n, const lq_pauli_term* terms, int nt, ExpParams* chunks,
+                     int max_chunks);
+int exp_chunk_count(const lq_pauli_term* terms, int nt);
+
+// <H> of nstates states (stride amplitudes apart) into out_dev[0..nstates);
+// partial holds expval_grid(n) * nstates doubles.
+lq_status expval_states(const double2* states, uint64_t stride, int nstates, int n,
+                        const lq_pauli_term* terms, int nt, double* partial, double* out_dev,
+                        cudaStream_t s);
+
+// --------------------------------------------------------------- launchers
+
+int sm_count();
+int expval_grid(int n);
+
+cudaError_t launch_init_basis(double2* amps, int n, uint64_t basis, cudaStream_t s);
+cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, int nstates,
+                        cudaStream_t s, const Patch* patches = nullptr);
+cudaError_t launch_psr_grad(const double* E, int np, double* out, cudaStream_t s);
+cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, double scale,
+                            cudaStream_t s);
+cudaError_t launch_bitrev(double2* state, int n, cudaStream_t s);
+cudaError_t fft_tables_init(cudaStream_t s);
+cudaError_t launch_expval(const ExpParams& E, const double2* state, uint64_t stride,
+                          int nstates, double* partial, double* out, int accumulate,
+                          cudaStream_t s);
+cudaError_t launch_apply_pauli_sum(const ExpParams& E, const double2* in, double2* out,
+                                   int accumulate, cudaStream_t s);
+
+}  // namespace lq

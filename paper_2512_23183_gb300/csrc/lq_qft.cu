@@ -1,0 +1,367 @@
+// lq_qft.cu -- the QFT of Sec. IV-B on the dense state, in FFT form (Alg. 2)
+// and gate form (Alg. 3).
+//
+// FFT form.  QFT|x> = N^{-1/2} sum_k e^{2 pi i x k/N}|k> is the unitary inverse
+// DFT.  Reading Alg. 3 per target qubit j: the controlled phases CP(pi/2^{j-q})
+// from every earlier qubit q < j are applied before H(j), so stage j is a
+// decimation-in-time butterfly on bit p = n-1-j,
+//     (a, b) -> (a + w_j b, a - w_j b),   w_j = exp(2 pi i M_j / 2^{j+1}),
+//     M_j = sum_{q<j} b_q 2^q   (b_q = bit n-1-q of the index),
+// with 1/sqrt2 per stage deferred to one final scale, followed by the bit
+// reversal of the index (the SWAPs).  Stages are grouped into shared-memory
+// passes over d consecutive qubits [q0, q1).  Inside a pass the twiddle factors
+// into a per-tile constant part (qubits q < q0 are fixed for the tile) and a
+// local part that depends only on in-tile bits; the constant parts of all d
+// stages commute to the start of the pass and form one diagonal
+//     D(V) = exp(2 pi i M_out V / 2^{q1}),  V = the group's bits as an integer,
+// applied by one table lookup and one complex multiply per amplitude
+// (four-step FFT).  Local twiddles come from a constant table in tangent form
+// (c, t = s/c) or cotangent form (s, u = c/s), so each butterfly costs
+// 6 FP64 FMAs: b' = b + i t b (2), a +- c b' (4).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "lq_device.cuh"
+#include "lq_internal.h"
+#include "lq_kernels.h"
+
+namespace lq {
+
+constexpr int FFT_MAX_D = 12;                     // qubits per pass
+constexpr int FFT_TABLE = (1 << FFT_MAX_D) - 1;   // sum_{r<12} 2^r entries
+
+// g_tw[(1 << r) - 1 + v] = (scale, ratio) of exp(2 pi i u / 2^{r+1}) for the
+// stage with r in-tile higher qubits, stored at v = bit-reverse_r(u).
+__device__ double2 g_tw[FFT_TABLE];
+
+__global__ void fft_table_kernel() {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= FFT_TABLE) return;
+  int r = 31 - __clz(idx + 1);
+  int v = idx + 1 - (1 << r);
+  int u = r ? (int)(__brev((unsigned)v) >> (32 - r)) : 0;
+  double s, c;
+  // angle 2 pi u / 2^{r+1} = pi * (u / 2^r)
+  sincospi((double)u / (double)(1 << r), &s, &c);
+  bool cot = (8 * u > (2 << r)) && (8 * u < 3 * (2 << r));
+  g_tw[idx] = cot ? make_double2(s, c / s) : make_double2(c, s / c);
+}
+
+cudaError_t fft_tables_init(cudaStream_t s) {
+  static int done_dev[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && done_dev[dev]) return cudaSuccess;
+  fft_table_kernel<<<(FFT_TABLE + 255) / 256, 256, 0, s>>>();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done_dev[dev] = 1;
+  return e;
+}
+
+struct FftParams {
+  int n, q0, q1, d, ms, plo, k;
+  int inverse;
+  double scale;   // folded into the diagonal (or applied alone)
+};
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) fft_pass_kernel(const FftParams F,
+                                                         double2* __restrict__ state) {
+  extern __shared__ double2 sm[];
+  __shared__ double2 omega[FFT_MAX_D];
+  const int k = F.k, ms = F.ms, d = F.d, plo = F.plo;
+  const uint32_t T = 1u << k;
+  double2* dtab = sm + T;                  // 2^d entries after the tile
+  const uint64_t ntiles = 1ull << (F.n - k);
+  const int nlow = plo - ms;               // CTA bits below the group: [ms, plo)
+  // sign flips for the inverse transform (conjugate twiddles), integer only
+  const uint32_t fpos = F.inverse ? 0x80000000u : 0u, fneg = fpos ^ 0x80000000u;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // CTA bits: low part -> [ms, plo), high part -> [plo + d, n)
+    const uint64_t tlo = t & ((1ull << nlow) - 1ull), thi = t >> nlow;
+    const uint64_t base = (tlo << ms) | (thi << (plo + d));
+    // M_out = sum_{q<q0} b_q 2^q over the high CTA bits: qubit q is bit n-1-q
+    uint64_t mout = 0;
+    for (int q = 0; q < F.q0; q++) mout |= ((base >> (F.n - 1 - q)) & 1ull) << q;
+    const bool diag = (mout != 0) || (F.scale != 1.0);
+    if (diag) {
+      // D(V) = scale * exp(sgn 2 pi i mout V / 2^{q1}), built by doubling from
+      // directly evaluated factors exp(sgn 2 pi i (mout 2^r mod 2^{q1}) / 2^{q1})
+      const uint64_t modmask = (F.q1 >= 64) ? ~0ull : ((1ull << F.q1) - 1ull);
+      if (threadIdx.x < (uint32_t)d) {
+        const uint64_t e = (mout << threadIdx.x) & modmask;
+        double s, c;
+        sincospi(2.0 * (double)e / (double)(1ull << F.q1), &s, &c);
+        omega[threadIdx.x] = make_double2(c, xsign(s, fpos));
+      }
+      if (threadIdx.x == 0) dtab[0] = make_double2(F.scale, 0.0);
+      __syncthreads();
+      for (int r = 0; r < d; r++) {
+        const double2 om = omega[r];
+        for (uint32_t v = threadIdx.x; v < (1u << r); v += BLOCK)
+          dtab[v | (1u << r)] = cmul(dtab[v], om.x, om.y);
+        __syncthreads();
+      }
+    }
+    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+      const uint64_t g = base | (s & ((1u << ms) - 1u)) | ((uint64_t)(s >> ms) << plo);
+      double2 v = state[g];
+      if (diag) {
+        const double2 w = dtab[s >> ms];
+        v = cmul(v, w.x, w.y);
+      }
+      sm[s] = v;
+    }
+    __syncthreads();
+    // stages: qubit j = q0 + r acts on local bit lp = ms + d - 1 - r
+    for (int r = 0; r < d; r++) {
+      const int lp = ms + d - 1 - r;
+      const double2* tw = g_tw + ((1 << r) - 1);
+      for (uint32_t j = threadIdx.x; j < (T >> 1); j += BLOCK) {
+        const uint32_t s0 = insert0(j, lp), s1 = s0 | (1u << lp);
+        const double2 a = sm[s0], b = sm[s1];
+        double2 o0, o1;
+        if (r == 0) {
+          o0 = make_double2(a.x + b.x, a.y + b.y);
+          o1 = make_double2(a.x - b.x, a.y - b.y);
+        } else {
+          const uint32_t v = s0 >> (lp + 1);
+          const double2 w = tw[v];
+          const uint32_t u = __brev(v) >> (32 - r);
+          const bool cot = (8u * u > (2u << r)) && (8u * u < 3u * (2u << r));
+          double tr, ti;
+          if (!cot) {  // w = c (1 + i t): b' = b + i t b
+            const double tt = xsign(w.y, fpos);
+            tr = fma(-tt, b.y, b.x);
+            ti = fma(tt, b.x, b.y);
+          } else {     // w = s (u + i): b' = u b + i b
+            tr = fma(w.y, b.x, xsign(b.y, fneg));
+            ti = fma(w.y, b.y, xsign(b.x, fpos));
+          }
+          o0 = make_double2(fma(w.x, tr, a.x), fma(w.x, ti, a.y));
+          o1 = make_double2(fma(-w.x, tr, a.x), fma(-w.x, ti, a.y));
+        }
+        sm[s0] = o0;
+        sm[s1] = o1;
+      }
+      __syncthreads();
+    }
+    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+      const uint64_t g = base | (s & ((1u << ms) - 1u)) | ((uint64_t)(s >> ms) << plo);
+      state[g] = sm[s];
+    }
+    __syncthreads();
+  }
+}
+
+static constexpr int kFftBlock = 256;
+
+cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, double scale,
+                            cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<kFftBlock>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((sizeof(double2) << MAX_TILE_BITS) +
+                                               (sizeof(double2) << FFT_MAX_D)));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  FftParams F;
+  F.n = n;
+  F.q0 = q0;
+  F.q1 = q1;
+  F.d = q1 - q0;
+  F.plo = n - q1;
+  F.ms = F.plo < 3 ? F.plo : 3;   // spectator low bits for coalesced loads
+  F.k = F.ms + F.d;
+  F.inverse = inverse;
+  F.scale = scale;
+  size_t smem = (sizeof(double2) << F.k) + (sizeof(double2) << F.d);
+  uint64_t ntiles = 1ull << (n - F.k);
+  int per_sm = smem <= 16384 ? 6 : smem <= 32768 ? 4 : smem <= 65536 ? 2 : 1;
+  uint64_t cap = (uint64_t)sm_count() * per_sm;
+  int grid = (int)(ntiles < cap ? ntiles : cap);
+  fft_pass_kernel<kFftBlock><<<grid, kFftBlock, smem, s>>>(F, state);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- bit reversal
+
+// In-place index bit reversal i -> rev_n(i).  Tile bits are the low L and the
+// high L bits; the middle bits M select the tile.  Tile c and tile rev_M(c)
+// exchange contents, so one CTA handles the pair (c <= rev_M(c)) and no tile
+// is read after another CTA wrote it.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) bitrev_kernel(double2* __restrict__ state, int n,
+                                                       int L) {
+  extern __shared__ double2 sm[];  // 2 * 2^{2L}
+  const int M = n - 2 * L;
+  const uint32_t TL = 1u << L, T = TL * TL;
+  double2* A = sm;
+  double2* B = sm + T;
+  const uint64_t ntiles = 1ull << M;
+  for (uint64_t c = blockIdx.x; c < ntiles; c += gridDim.x) {
+    const uint64_t cr = M ? (__brevll(c) >> (64 - M)) : 0;
+    if (cr < c) continue;
+    // element (hi, lo) of tile c: index hi << (n-L) | c << L | lo; slot hi*TL+lo
+    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+      const uint64_t hi = s >> L, lo = s & (TL - 1);
+      A[s] = state[(hi << (n - L)) | (c << L) | lo];
+      if (cr != c) B[s] = state[(hi << (n - L)) | (cr << L) | lo];
+    }
+    __syncthreads();
+    // destination (hi', lo') of tile cr receives source (hi = rev(lo'), lo = rev(hi'))
+    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+      const uint32_t hi2 = s >> L, lo2 = s & (TL - 1);
+      const uint32_t src = ((__brev(lo2) >> (32 - L)) << L) | (__brev(hi2) >> (32 - L));
+      state[((uint64_t)hi2 << (n - L)) | (cr << L) | lo2] = A[src];
+      if (cr != c) state[((uint64_t)hi2 << (n - L)) | (c << L) | lo2] = B[src];
+    }
+    __syncthreads();
+  }
+}
+
+// Small states: the whole vector in one CTA.
+__global__ void bitrev_small_kernel(double2* __restrict__ state, int n) {
+  extern __shared__ double2 sm[];
+  const uint32_t N = 1u << n;
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) sm[i] = state[i];
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
+    state[i] = sm[n ? (__brev(i) >> (32 - n)) : 0];
+}
+
+cudaError_t launch_bitrev(double2* state, int n, cudaStream_t s) {
+  if (n <= 12) {
+    static bool conf = false;
+    if (!conf) {
+      cudaError_t e = cudaFuncSetAttribute(bitrev_small_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(sizeof(double2) << 12));
+      if (e != cudaSuccess) return e;
+      conf = true;
+    }
+    bitrev_small_kernel<<<1, 512, sizeof(double2) << n, s>>>(state, n);
+    return cudaGetLastError();
+  }
+  const int L = 5;
+  size_t smem = 2 * (sizeof(double2) << (2 * L));
+  uint64_t ntiles = 1ull << (n - 2 * L);
+  uint64_t cap = (uint64_t)sm_count() * 4;
+  int grid = (int)(ntiles < cap ? ntiles : cap);
+  bitrev_kernel<256><<<grid, 256, smem, s>>>(state, n, L);
+  return cudaGetLastError();
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+// Pass boundaries (qubit indices) of the FFT form: the lowest group takes up to
+// 12 qubits, earlier groups up to 10 (tile = group + 3 spectator bits <= 13).
+static std::vector<int> fft_bounds(int n) {
+  std::vector<int> bounds;
+  int rest = n;
+  int last = n < 12 ? n : 12;
+  rest -= last;
+  int ng = (rest + 9) / 10;
+  bounds.push_back(0);
+  for (int i = 0; i < ng; i++)
+    bounds.push_back(bounds.back() + (rest - bounds.back() + (ng - i) - 1) / (ng - i));
+  if (bounds.back() != n) bounds.push_back(n);
+  return bounds;
+}
+
+static std::vector<lq_gate> qft_gate_list(int n, int inverse) {
+  const double PI = 3.14159265358979323846;
+  std::vector<lq_gate> g;
+  auto mk = [](int kind, int a, int b, double ang) {
+    lq_gate G;
+    std::memset(&G, 0, sizeof G);
+    G.kind = kind;
+    G.qubits[0] = a;
+    G.qubits[1] = b;
+    G.qubits[2] = -1;
+    G.param = -1;
+    G.angle = ang;
+    return G;
+  };
+  for (int i = 0; i < n; i++) {
+    g.push_back(mk(LQ_H, i, -1, 0));
+    for (int j = i + 1; j < n; j++) g.push_back(mk(LQ_CP, i, j, PI / std::ldexp(1.0, j - i)));
+  }
+  for (int i = 0; i < n / 2; i++) g.push_back(mk(LQ_SWAP, i, n - 1 - i, 0));
+  if (inverse) {
+    std::vector<lq_gate> r(g.rbegin(), g.rend());
+    for (auto& G : r)
+      if (G.kind == LQ_CP) G.angle = -G.angle;
+    g.swap(r);
+  }
+  return g;
+}
+
+extern "C" lq_status lq_qft_plan(int n, int method, lq_plan_info* out) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
+  if (method == LQ_QFT_GATES) {
+    std::vector<lq_gate> g = qft_gate_list(n, 0);
+    return lq_circuit_plan(n, g.data(), (int)g.size(), nullptr, 0, out);
+  }
+  if (method != LQ_QFT_FFT) return fail(LQ_ERR_INVALID_ARG, "unknown QFT method %d", method);
+  std::vector<int> b = fft_bounds(n);
+  const double N = std::ldexp(1.0, n);
+  double fl = 0;
+  int kmax = 0;
+  for (std::size_t p = 0; p + 1 < b.size(); p++) {
+    int d = b[p + 1] - b[p];
+    int ms = (n - b[p + 1]) < 3 ? (n - b[p + 1]) : 3;
+    kmax = kmax > d + ms ? kmax : d + ms;
+    // butterflies: first stage 2 adds per amplitude, others 6 FMA per pair
+    fl += N * (2.0 + 6.0 * (d - 1));
+    // diagonal of the pass (all but the first; the last also carries the scale)
+    if (p > 0 || b.size() == 2) fl += 6.0 * N;
+  }
+  out->npasses = (int)b.size();   // FFT passes + the bit-reversal pass
+  out->tile_bits = kmax;
+  out->dp_flops = fl;
+  out->dram_bytes = 32.0 * N * (double)b.size();
+  return LQ_OK;
+}
+
+extern "C" lq_status lq_qft(void* amps, int n, int inverse, int method, void* scratch,
+                            size_t scratch_bytes, lq_stream stream) {
+  (void)scratch;
+  (void)scratch_bytes;
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!amps) return fail(LQ_ERR_INVALID_ARG, "amps is NULL");
+  if (method != LQ_QFT_FFT && method != LQ_QFT_GATES)
+    return fail(LQ_ERR_INVALID_ARG, "unknown QFT method %d", method);
+  cudaStream_t s = (cudaStream_t)stream;
+  double2* psi = (double2*)amps;
+  if (method == LQ_QFT_GATES) {
+    // Alg. 3: for i: H(i), CP(pi/2^{j-i}) control i target j > i; then the
+    // swaps.  The inverse is the reversed sequence with conjugated phases.
+    std::vector<lq_gate> g = qft_gate_list(n, inverse);
+    return lq_apply_circuit(amps, n, g.data(), (int)g.size(), nullptr, 0, stream);
+  }
+  cudaError_t e = fft_tables_init(s);
+  if (e != cudaSuccess) return fail(LQ_ERR_CUDA, "fft tables: %s", cudaGetErrorString(e));
+  std::vector<int> bounds = fft_bounds(n);
+  const double scale = std::ldexp(1.0, -n / 2) * ((n & 1) ? 0.70710678118654752440 : 1.0);
+  int npass = (int)bounds.size() - 1;
+  for (int p = 0; p < npass; p++) {
+    e = launch_fft_pass(psi, n, bounds[p], bounds[p + 1], inverse,
+                        p == npass - 1 ? scale : 1.0, s);
+    if (e != cudaSuccess) return fail(LQ_ERR_CUDA, "fft pass: %s", cudaGetErrorString(e));
+  }
+  e = launch_bitrev(psi, n, s);
+  if (e != cudaSuccess) return fail(LQ_ERR_CUDA, "bit reversal: %s", cudaGetErrorString(e));
+  return LQ_OK;
+}

@@ -1,0 +1,254 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: 1e-12 absolute per amplitude; energies and gradients within
+1e-10 * max(1, |value|); permutation-only circuits and basis-state set-up
+bit-exact.  Sizes span one tile (n <= 10), several tiles (n = 11..17) and
+the edge cases n = 1, n below the contiguous-run width, and n = tile width.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ATOL = 1e-12
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lq():
+    import paper_2512_23183_gb300 as m
+
+    m.load()
+    return m
+
+
+def dev(psi):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+
+
+def host(t):
+    import torch
+
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def close_e(a, b):
+    return abs(a - b) <= RTOL * max(1.0, abs(b))
+
+
+# --------------------------------------------------------------- states
+
+@pytest.mark.parametrize("n", [1, 2, 5, 10, 13, 20])
+def test_state_init_bit_exact(lq, n):
+    x = W.basis_index(n, 7)
+    t = lq.new_state(n, x)
+    np.testing.assert_array_equal(host(t), oracle.basis_state(n, x))
+
+
+def test_paper_worked_examples(lq):
+    s = np.zeros(4, complex)
+    s[0] = s[3] = 1 / np.sqrt(2)
+    t = dev(s)
+    lq.apply_circuit(t, 2, [W.G("CNOT", 0, 1)])
+    np.testing.assert_array_equal(host(t), oracle.cnot_alg1(s.copy(), 2, 0, 1))
+    s = np.zeros(8, complex)
+    s[5] = s[6] = 1 / np.sqrt(2)
+    t = dev(s)
+    lq.apply_circuit(t, 3, [W.G("CCX", 0, 1, 2)])
+    np.testing.assert_array_equal(host(t), oracle.toffoli_alg4(s.copy(), 3, 0, 1, 2))
+
+
+# ------------------------------------------------------------- circuits
+
+@pytest.mark.parametrize("n,seed,ng", [(1, 1, 30), (2, 2, 40), (3, 3, 60), (4, 4, 80), (6, 5, 80),
+                                       (9, 6, 80), (10, 7, 100), (11, 8, 100), (12, 9, 80),
+                                       (14, 10, 80), (17, 11, 60)])
+def test_random_circuit(lq, n, seed, ng):
+    rng = np.random.default_rng(seed)
+    gates, P = W.random_circuit(n, ng, rng)
+    params = rng.uniform(-np.pi, np.pi, P)
+    psi = W.gaussian_state(n, 100 + seed)
+    want = oracle.apply_circuit(psi.copy(), n, gates, params)
+    t = dev(psi)
+    lq.apply_circuit(t, n, gates, params)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
+
+
+@pytest.mark.parametrize("name", sorted(oracle.GATE_CODES))
+def test_each_gate_kind_on_every_qubit_tuple(lq, name):
+    n = 4
+    rng = np.random.default_rng(abs(hash(name)) % 1000)
+    k = 3 if name == "CCX" else 2 if name in (
+        "CNOT", "CY", "CZ", "CP", "SWAP", "CRX", "CRY", "CRZ", "RXX", "RYY", "RZZ", "U2") else 1
+    import itertools
+
+    gates = []
+    for qs in itertools.permutations(range(n), k):
+        mat = None
+        if name in ("U1", "U2"):
+            d = 2 if name == "U1" else 4
+            q, _ = np.linalg.qr(rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d)))
+            mat = q
+        gates.append(W.G(name, *qs, angle=float(rng.uniform(-7, 7)), mat=mat))
+    psi = W.gaussian_state(n, 3)
+    for g in gates:
+        want = oracle.apply_circuit(psi.copy(), n, [g])
+        t = dev(psi)
+        lq.apply_circuit(t, n, [g])
+        np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL, err_msg=str(g))
+
+
+@pytest.mark.parametrize("n,depth,ent", [(10, 4, "ladder"), (16, 3, "ring"), (20, 2, "ladder")])
+def test_hea(lq, n, depth, ent):
+    gates, P = W.hea(n, depth, ent)
+    th = W.angles(P, 5)
+    want = oracle.apply_circuit(oracle.basis_state(n), n, gates, th)
+    t = lq.new_state(n)
+    lq.apply_circuit(t, n, gates, th)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
+
+
+def test_permutation_circuit_bit_exact(lq):
+    n = 15
+    rng = np.random.default_rng(3)
+    gates, _ = W.random_circuit(n, 200, rng, kinds=["X", "Y", "Z", "S", "SDG", "CNOT", "CY", "CZ",
+                                                     "SWAP", "CCX"])
+    psi = W.gaussian_state(n, 4)
+    want = oracle.apply_circuit(psi.copy(), n, gates)
+    t = dev(psi)
+    lq.apply_circuit(t, n, gates)
+    np.testing.assert_array_equal(host(t), want)
+
+
+def test_long_circuit_rescales(lq):
+    # thousands of tangent-form rotations: the deferred scalar is renormalised
+    n = 6
+    rng = np.random.default_rng(9)
+    gates = [W.G("RX", q % n, angle=float(rng.uniform(1.2, 1.9))) for q in range(3000)]
+    psi = W.gaussian_state(n, 1)
+    want = oracle.apply_circuit(psi.copy(), n, gates)
+    t = dev(psi)
+    lq.apply_circuit(t, n, gates)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=1e-11)
+
+
+# ----------------------------------------------------------------- <H>
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (3, 2), (8, 3), (12, 4), (16, 5), (20, 6)])
+def test_expval(lq, n, seed):
+    rng = np.random.default_rng(seed)
+    terms = W.random_pauli_sum(n, 50, rng, kmin=1, kmax=min(4, n))
+    if n >= 2:
+        terms += W.heisenberg(n, ring=n > 2)
+    psi = W.gaussian_state(n, seed)
+    want = oracle.expval(psi, n, terms)
+    got = lq.expval_pauli_sum(dev(psi), n, terms)
+    assert close_e(got, want), (got, want)
+
+
+def test_expval_many_terms_chunked(lq):
+    n = 9
+    rng = np.random.default_rng(11)
+    terms = W.random_pauli_sum(n, 1500, rng, kmin=1, kmax=5)
+    psi = W.gaussian_state(n, 2)
+    assert close_e(lq.expval_pauli_sum(dev(psi), n, terms), oracle.expval(psi, n, terms))
+    assert lq.expval_pauli_sum(dev(psi), n, []) == 0.0
+
+
+@pytest.mark.parametrize("n", [2, 7, 13])
+def test_apply_pauli_sum(lq, n):
+    import torch
+
+    rng = np.random.default_rng(n)
+    terms = W.random_pauli_sum(n, 30, rng, kmin=1, kmax=min(3, n))
+    psi = W.gaussian_state(n, 8)
+    want = np.zeros_like(psi)
+    for c, s in terms:
+        gs = [W.G(ch, q) for q, ch in enumerate(s) if ch != "I"]
+        want += c * oracle.apply_circuit(psi.copy(), n, gs)
+    out = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+    lq.apply_pauli_sum(out, dev(psi), n, terms)
+    np.testing.assert_allclose(host(out), want, rtol=0, atol=ATOL * 10)
+
+
+# ------------------------------------------------------------------ QFT
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 11, 12, 13, 14, 17, 20])
+def test_qft_fft_gaussian(lq, n):
+    psi = W.gaussian_state(n, 1000 + n)
+    want = oracle.qft_fft(psi.copy(), n)
+    t = dev(psi)
+    lq.qft(t, n)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
+    lq.qft(t, n, inverse=True)
+    np.testing.assert_allclose(host(t), psi, rtol=0, atol=ATOL)
+
+
+@pytest.mark.parametrize("n", [1, 4, 9, 12, 15])
+def test_qft_gate_form(lq, n):
+    psi = W.gaussian_state(n, 2000 + n)
+    want = oracle.qft_gates(psi.copy(), n)
+    t = dev(psi)
+    lq.qft(t, n, method=lq.QFT_GATES)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
+    lq.qft(t, n, inverse=True, method=lq.QFT_GATES)
+    np.testing.assert_allclose(host(t), psi, rtol=0, atol=ATOL)
+
+
+@pytest.mark.parametrize("n", [22, 24])
+def test_qft_basis_closed_form_sampled(lq, n):
+    N = 1 << n
+    x = W.basis_index(n, 2000 + n)
+    t = lq.new_state(n, x)
+    lq.qft(t, n)
+    got = host(t)
+    k = np.random.default_rng(n).integers(0, N, 4096)
+    want = np.exp(2j * np.pi * ((x * k) % N) / N) / np.sqrt(N)
+    np.testing.assert_allclose(got[k], want, rtol=0, atol=ATOL)
+
+
+# ------------------------------------------------------------ gradients
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("n,depth,ent", [(1, 2, "ladder"), (4, 3, "ring"), (10, 4, "ladder"),
+                                         (12, 2, "ring")])
+def test_param_shift(lq, method, n, depth, ent):
+    gates, P = W.hea(n, depth, ent)
+    th = W.angles(P, 1 + n)
+    terms = W.heisenberg(n) if n > 1 else [(1.0, "Z"), (0.5, "X")]
+    e_w, g_w = oracle.param_shift(n, gates, th, terms)
+    e, g = lq.param_shift_grad(n, gates, th, terms, method=method)
+    assert close_e(e, e_w)
+    np.testing.assert_allclose(g, g_w, rtol=0, atol=RTOL * max(1.0, np.abs(g_w).max()))
+
+
+def test_param_shift_all_two_term_kinds(lq):
+    n = 4
+    gates = [W.G("H", 0), W.G("RX", 0, param=0), W.G("RY", 1, param=1), W.G("RZ", 2, param=2),
+             W.G("P", 3, param=3), W.G("CNOT", 0, 2), W.G("CP", 1, 3, param=4),
+             W.G("RXX", 0, 3, param=5), W.G("RYY", 2, 1, param=6), W.G("RZZ", 3, 0, param=7)]
+    th = W.angles(8, 17)
+    terms = W.random_pauli_sum(n, 20, np.random.default_rng(5), kmin=1, kmax=4)
+    e_w, g_w = oracle.param_shift(n, gates, th, terms)
+    for method in (0, 1):
+        e, g = lq.param_shift_grad(n, gates, th, terms, method=method)
+        assert close_e(e, e_w)
+        np.testing.assert_allclose(g, g_w, rtol=0, atol=RTOL)
+
+
+# -------------------------------------------------------------- Trotter
+
+@pytest.mark.parametrize("n,steps", [(3, 5), (8, 12), (12, 4)])
+def test_trotter(lq, n, steps):
+    static, field, A, omega, x0 = W.xyz_trotter(n, J=(1.0, 0.7, 0.4))
+    dt = 0.07
+    want = oracle.trotter(oracle.basis_state(n, x0), n, static, field, A, omega, dt, steps)
+    t = lq.new_state(n, x0)
+    lq.trotter_evolve(t, n, static, field, A, omega, dt, steps)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
