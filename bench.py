@@ -1,0 +1,525 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 dense state-vector hot path (arXiv 2512.23183 method).
+
+One step runs every row of the hot path once:
+  a1  state set-up: the synthetic input state is copied into the working state
+  a2-a4  one hardware-efficient layer (RY, RZ on every qubit, CNOT ladder),
+      lowered to fused shared-memory tile passes
+  a5  QFT, FFT form (Alg. 2)
+  a6  inverse QFT, gate form (Alg. 3)
+  a7  <H> of the open-chain XYZ Heisenberg model
+  a8  batched parameter-shift energy + gradient of the n=10, depth-4 VQE
+      problem (161 circuits in shared memory)
+  a9  adjoint energy + gradient of the same VQE problem (when built)
+on an n-qubit complex128 state (default n = 30: 16 GiB, inputs larger than L2,
+so no flush is needed).  `value` is the step's algorithmic state-vector bytes
+(32 B per amplitude per pass, 16 B per amplitude for <H>) divided by the step
+time measured with CUDA events; `e2e` is the same step through the library's
+public API with the input state copied from pinned host memory and the energy
+read back inside the timed region.
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas (no
+collective on the data path); value = all ranks' bytes / max rank time.
+`--impl reference` times the CPU oracle on a bounded sample of the same step.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "state-vector HBM GB/s (% peak); VQE grads/s plain vs batched; serve p50/p99"
+UNIT = "GB/s"
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_MEASURED_TFLOPS = 1.19  # DFMA microbenchmark on the GB300s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lq", choices=["lq", "reference"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--no-extras", action="store_true", help="skip the VQE/serve side measurements")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=23, help="qubits of the bounded oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel sources are unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in rec.get("sources", []):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return rec.get("bytes_per_launch") if h.hexdigest() == rec.get("sha256") else None
+
+
+# -------------------------------------------------------------- the step
+
+class Step:
+    """All hot-path rows on an n-qubit state (see module docstring)."""
+
+    def __init__(self, n, device):
+        import numpy as np
+        import torch
+
+        import paper_2512_23183_gb300 as lq
+        import workloads as W
+
+        self.lq, self.n, self.dev = lq, n, device
+        g = torch.Generator(device=device)
+        g.manual_seed(1000 + n)
+        v = torch.randn(2 << n, dtype=torch.float64, device=device, generator=g)
+        self.inp = torch.view_as_complex(v.view(-1, 2))
+        self.inp /= torch.linalg.vector_norm(self.inp)
+        del v
+        self.work = torch.empty_like(self.inp)
+        self.layer, P = W.hea(n, 1, "ladder")
+        self.theta = W.angles(P, 2000 + n)
+        self.terms = W.heisenberg(n)
+        self.exp_ws = torch.empty(lq.load().lq_expval_workspace_size(n, len(self.terms)),
+                                  dtype=torch.uint8, device=device)
+        self.e_dev = torch.zeros(1, dtype=torch.float64, device=device)
+        self.packed_terms = lq.pack_terms(self.terms, n)
+        # a8/a9: VQE problem, n=10, depth 4, 80 parameters
+        self.vn = 10
+        self.vgates, self.vth, self.vterms = W.vqe_chain(10, 4, 1)
+        self.psr_ws = torch.empty(lq.load().lq_param_shift_workspace_size(10, len(self.vth),
+                                                                          len(self.vterms), 1),
+                                  dtype=torch.uint8, device=device)
+        self.has_adjoint = True
+        try:
+            lq.adjoint_grad(10, self.vgates, self.vth, self.vterms, device=device)
+        except lq.LqError:
+            self.has_adjoint = False
+        plan_l = lq.circuit_plan(n, self.layer, self.theta)
+        plan_f = lq.qft_plan(n, lq.QFT_FFT)
+        plan_g = lq.qft_plan(n, lq.QFT_GATES)
+        N = float(1 << n)
+        self.rows = {
+            "a1_init": dict(bytes=32 * N, flops=0.0, launches=0),
+            "a2_a4_hea_layer": dict(bytes=plan_l["dram_bytes"], flops=plan_l["dp_flops"],
+                                    launches=plan_l["npasses"], kernel="pass_kernel"),
+            "a5_qft_fft": dict(bytes=plan_f["dram_bytes"], flops=plan_f["dp_flops"],
+                               launches=plan_f["npasses"], kernel="fft_pass_kernel"),
+            "a6_qft_gates_inverse": dict(bytes=plan_g["dram_bytes"], flops=plan_g["dp_flops"],
+                                         launches=plan_g["npasses"], kernel="pass_kernel"),
+            "a7_expval": dict(bytes=16 * N, flops=self._expval_flops(), launches=2,
+                              kernel="expval_kernel"),
+            "a8_psr_batched_n10": dict(bytes=0.0, flops=0.0, launches=4),
+        }
+        if self.has_adjoint:
+            self.rows["a9_adjoint_n10"] = dict(bytes=0.0, flops=0.0, launches=0)
+        self.bytes = sum(r["bytes"] for r in self.rows.values())
+
+    def _expval_flops(self):
+        # per X group: 4 FP64 ops per pair (vr, vi) + 1 FMA per term; diagonal
+        # group: |psi|^2 + 1 FMA per term (FMA = 2 flops)
+        groups = {}
+        for c, s in self.terms:
+            x = "".join("1" if ch in "XY" else "0" for ch in s)
+            groups[x] = groups.get(x, 0) + 1
+        N = float(1 << self.n)
+        fl = 0.0
+        for x, cnt in groups.items():
+            if "1" in x:
+                fl += (N / 2) * (6 + 2 * cnt)
+            else:
+                fl += N * (3 + 2 * cnt)
+        return fl
+
+    def run(self, events=None, host_in=None):
+        """One step; `events` (list of CUDA events, len 8) marks the rows.
+        host_in: pinned host tensor to copy in (e2e)."""
+        import ctypes
+
+        import torch
+
+        lq, n = self.lq, self.n
+        s = torch.cuda.current_stream()
+        ev = events or [None] * 8
+
+        def mark(i):
+            if ev[i] is not None:
+                ev[i].record(s)
+
+        mark(0)
+        if host_in is not None:
+            self.work.copy_(host_in, non_blocking=True)
+        else:
+            self.work.copy_(self.inp)
+        mark(1)
+        lq.apply_circuit(self.work, n, self.layer, self.theta)
+        mark(2)
+        lq.qft(self.work, n, method=lq.QFT_FFT)
+        mark(3)
+        lq.qft(self.work, n, inverse=True, method=lq.QFT_GATES)
+        mark(4)
+        lq._check(lq.load().lq_expval_pauli_sum_async(
+            lq._ptr(self.work), n, self.packed_terms, len(self.terms),
+            ctypes.c_void_p(self.e_dev.data_ptr()), lq._ptr(self.exp_ws), self.exp_ws.numel(),
+            ctypes.c_void_p(s.cuda_stream)))
+        mark(5)
+        e8, g8 = lq.param_shift_grad(self.vn, self.vgates, self.vth, self.vterms,
+                                     method=lq.PSR_BATCHED, workspace=self.psr_ws)
+        mark(6)
+        if self.has_adjoint:
+            lq.adjoint_grad(self.vn, self.vgates, self.vth, self.vterms, device=self.dev)
+        mark(7)
+        return e8, g8
+
+
+def bench_lq(a, rank, world, device):
+    import torch
+
+    import paper_2512_23183_gb300 as lq
+
+    lq.load()
+    step = Step(a.n, device)
+    for _ in range(a.warmup):
+        step.run()
+    torch.cuda.synchronize()
+    names = list(step.rows)
+    seg_ms = {k: 0.0 for k in names}
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(a.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else int(os.environ.get("LOCAL_RANK", 0)))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record()
+    for k in range(a.steps):
+        step.run(evs[k])
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t0.elapsed_time(t1)
+    for k in range(a.steps):
+        e = evs[k]
+        for i, nm in enumerate(names):
+            if i + 1 < 8:
+                seg_ms[nm] += e[i].elapsed_time(e[i + 1])
+    ms = total_ms / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * step.bytes / (ms * 1e-3) / 1e9
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    rows = {}
+    for nm in names:
+        r = step.rows[nm]
+        t = seg_ms[nm] / a.steps
+        rows[nm] = dict(ms=round(t, 3), gbs=round(r["bytes"] / (t * 1e-3) / 1e9, 1) if t else None,
+                        fp64_tflops=round(r["flops"] / (t * 1e-3) / 1e12, 4) if t else None,
+                        launches=r["launches"])
+    # dominant kernel: the kernel family with the largest share of the step
+    fam = {}
+    for nm in names:
+        kern = step.rows[nm].get("kernel")
+        if kern:
+            f = fam.setdefault(kern, dict(ms=0.0, flops=0.0, bytes=0.0, launches=0))
+            f["ms"] += seg_ms[nm] / a.steps
+            f["flops"] += step.rows[nm]["flops"]
+            f["bytes"] += step.rows[nm]["bytes"]
+            f["launches"] += step.rows[nm]["launches"]
+    dom = max(fam, key=lambda k: fam[k]["ms"])
+    f = fam[dom]
+    per_launch_s = f["ms"] * 1e-3 / max(f["launches"], 1)
+    flops_pl = f["flops"] / max(f["launches"], 1)
+    bytes_pl = f["bytes"] / max(f["launches"], 1)
+    ach_tf = flops_pl / per_launch_s / 1e12
+    ach_gbs = bytes_pl / per_launch_s / 1e9
+    roofline = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4),
+                "traffic": profiled_traffic(dom), "kernel": dom,
+                "peak_note": "FP64 nominal (recipe); DFMA microbenchmark measured %.2f"
+                             % FP64_MEASURED_TFLOPS,
+                "hbm": {"achieved_gbs": round(ach_gbs, 1), "peak_gbs": hbm_peak,
+                        "frac": round(ach_gbs / hbm_peak, 4),
+                        "algorithmic_bytes_per_launch": bytes_pl},
+                "algorithmic_flops_per_launch": flops_pl}
+    kernels = {k: dict(ms_per_step=round(v["ms"], 3), launches=v["launches"],
+                       fp64_tflops=round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 4),
+                       hbm_gbs=round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1))
+               for k, v in fam.items()}
+    launches = sum(r["launches"] for r in step.rows.values())
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "sv_step_n%d" % a.n, "n_qubits": a.n,
+                   "state_bytes": 16 << a.n, "input": "complex Gaussian from seed %d (torch cuda "
+                   "generator), L2-normalised" % (1000 + a.n),
+                   "rows": "a1 copy-in, a2-a4 HEA layer, a5 FFT-QFT, a6 gate-QFT^-1, a7 <H> "
+                           "XYZ chain; a8 batched PSR + a9 adjoint of HEA n=10 d=4 (80 params)",
+                   "l2": "inputs larger than L2 (state %d GiB), no flush" % ((16 << a.n) >> 30)
+                   if a.n >= 24 else "state smaller than L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "hbm_frac": round(value / hbm_peak, 4),
+        "rows": rows, "kernels": kernels, "roofline": roofline,
+        "gpu_launches": launches * a.steps,
+        "clocks": clk,
+    }
+    if not a.no_e2e and rank == 0:
+        out["e2e"] = e2e(step, a)
+    return out, step
+
+
+def e2e(step, a):
+    """Same step through the public API with host buffers: the input state
+    is copied from pinned host memory and the energy read back each step."""
+    import torch
+
+    host = torch.empty(step.inp.shape, dtype=step.inp.dtype, pin_memory=True)
+    host.copy_(step.inp)
+    out_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
+    for _ in range(2):
+        step.run(host_in=host)
+        out_host.copy_(step.e_dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    k = max(2, a.steps // 2)
+    for _ in range(k):
+        step.run(host_in=host)
+        out_host.copy_(step.e_dev)   # synchronous device->host read of <H>
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / k
+    del host
+    return {"value": round(step.bytes / dt / 1e9, 2), "unit": UNIT,
+            "h2d_bytes_per_step": int(step.inp.numel() * 16), "d2h_bytes_per_step": 8 + 8 * 81,
+            "ms_per_step": round(dt * 1e3, 3)}
+
+
+# ------------------------------------------------------- side measurements
+
+def vqe_extras(device):
+    """Gradients per second, plain (per-circuit library calls) vs batched,
+    on the n=10 depth-4 ladder problem and the n=16 depth-8 ring problem."""
+    import torch
+
+    import paper_2512_23183_gb300 as lq
+    import workloads as W
+
+    res = {}
+    for name, (gates, th, terms, n, reps_p, reps_b) in {
+        "vqe_n10_d4_80p": W.vqe_chain(10, 4, 1) + (10, 2, 10),
+        "vqe_n16_d8_ring_256p": W.vqe_ring(16, 8, 3) + (16, 1, 3),
+    }.items():
+        r = {}
+        for meth, reps in ((lq.PSR_PLAIN, reps_p), (lq.PSR_BATCHED, reps_b)):
+            ws = torch.empty(lq.load().lq_param_shift_workspace_size(n, len(th), len(terms), meth),
+                             dtype=torch.uint8, device=device)
+            lq.param_shift_grad(n, gates, th, terms, method=meth, workspace=ws)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                lq.param_shift_grad(n, gates, th, terms, method=meth, workspace=ws)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / reps
+            r["plain" if meth == 0 else "batched"] = {"grads_per_s": round(1.0 / dt, 3),
+                                                      "ms": round(dt * 1e3, 3)}
+            del ws
+        try:
+            lq.adjoint_grad(n, gates, th, terms, device=device)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps_b):
+                lq.adjoint_grad(n, gates, th, terms, device=device)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / reps_b
+            r["adjoint"] = {"grads_per_s": round(1.0 / dt, 3), "ms": round(dt * 1e3, 3)}
+        except lq.LqError:
+            pass
+        r["circuits_per_grad"] = 2 * len(th) + 1
+        res[name] = r
+    return res
+
+
+# ----------------------------------------------------------- CPU baseline
+
+def oracle_sample_rate(n):
+    """The oracle, as it stands, on the same step at n qubits: returns
+    (GB/s by the step's algorithmic-bytes formula, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+
+    oracle.build()
+    psi0 = W.gaussian_state(n, 1000 + n)
+    layer, P = W.hea(n, 1, "ladder")
+    th = W.angles(P, 2000 + n)
+    terms = W.heisenberg(n)
+    t0 = time.perf_counter()
+    work = psi0.copy()                                   # a1
+    oracle.apply_circuit(work, n, layer, th)             # a2-a4
+    oracle.qft_fft(work, n)                              # a5
+    oracle.qft_gates(work, n)                            # a6 (forward gate form, same cost)
+    e = oracle.expval(work, n, terms)                    # a7
+    dt = time.perf_counter() - t0
+    import paper_2512_23183_gb300 as lq                  # plan only (host): byte accounting
+
+    N = float(1 << n)
+    byts = (32 * N + lq.circuit_plan(n, layer, th)["dram_bytes"] + lq.qft_plan(n, 0)["dram_bytes"]
+            + lq.qft_plan(n, 1)["dram_bytes"] + 16 * N)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    del e, np
+    return byts / dt / 1e9, dt, threads
+
+
+def cpu_baseline(n):
+    gbs, dt, threads = oracle_sample_rate(n)
+    return {"value": round(gbs, 3), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "one step (a1-a7) at n=%d (%.1f s of CPU work; a8/a9 excluded), "
+                      "same algorithmic-bytes formula" % (n, dt)}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return None
+    n = a.cpu_n - 2
+    for _ in range(a.warmup):
+        oracle_sample_rate(n)
+    rates, times = [], []
+    for _ in range(a.steps):
+        g, dt, threads = oracle_sample_rate(n)
+        rates.append(g)
+        times.append(dt)
+    value = sum(rates) / len(rates)
+    ms = 1e3 * sum(times) / len(times)
+    return {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "sv_step_n%d" % a.n,
+                       "sample": "oracle step a1-a7 at n=%d per step" % n},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": threads,
+                             "kind": "oracle", "sample": "step a1-a7 at n=%d" % n},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if a.impl == "reference":
+        out = run_reference(a, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    device = "cuda:%d" % local
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device(device))
+    out, step = bench_lq(a, rank, world, device)
+    del step
+    torch.cuda.empty_cache()
+    if rank == 0:
+        if not a.no_extras:
+            out["vqe"] = vqe_extras(device)
+        out["cpu_baseline"] = cpu_baseline(a.cpu_n)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,275 @@
+// lq_adjoint.cu -- exact gradients by reverse-mode (adjoint) differentiation.
+//
+// For E(theta) = <psi_L|H|psi_L>, psi_L = U_L ... U_1 |0>, and a gate
+// U_k = exp(-i theta G_k / 2) (Sec. III-A form of the parametrised gates):
+//     dE/dtheta_k = 2 Re <lambda_k| (-i G_k / 2) |psi_k> = Im <lambda_k|G_k|psi_k>,
+// where psi_k = U_k ... U_1|0> and lambda_k = U_{k+1}^dag ... U_L^dag H psi_L.
+// Starting from psi_L and lambda_L = H psi_L, the sweep for k = L..1 adds
+// Im <lambda|G_k|psi> to the gradient of gate k's parameter and then applies
+// U_k^dag to both states.  Phase gates P(theta) = exp(i theta |1><1|) and
+// CP have G = -2 (projector), controlled rotations G = |1><1| (x) sigma.
+//
+// The sweep is lowered like a circuit: each U_k^dag becomes tile ops in
+// tangent form with deferred scalars (the same scalar for both states, so
+// <lambda|G|psi> carries the real factor |zeta|^2), and each gradient term
+// becomes an OP_GRAD op reduced per tile; two-state tile passes hold psi and
+// lambda in shared memory together, so each pass reads and writes each
+// state once.  Two states are resident, no checkpoints are needed: U^dag
+// uncomputes the forward states.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lq_coefs.h"
+#include "lq_internal.h"
+#include "lq_kernels.h"
+
+namespace lq {
+
+#define LQ_CUDA(expr)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      (void)cudaGetLastError();                                                        \
+      return fail(LQ_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                           \
+    }                                                                                  \
+  } while (0)
+
+static inline std::size_t align256(std::size_t b) { return (b + 255) & ~(std::size_t)255; }
+
+// U^dag of a gate: rotations and phases at -theta, S <-> SDG, T <-> TDG,
+// matrices conjugate-transposed, the rest self-inverse.
+static lq_gate inverse_gate(const lq_gate& g) {
+  lq_gate r = g;
+  switch (g.kind) {
+    case LQ_S: r.kind = LQ_SDG; break;
+    case LQ_SDG: r.kind = LQ_S; break;
+    case LQ_T: r.kind = LQ_TDG; break;
+    case LQ_TDG: r.kind = LQ_T; break;
+    case LQ_U1: case LQ_U2: {
+      int d = g.kind == LQ_U1 ? 2 : 4;
+      for (int i = 0; i < d; i++)
+        for (int j = 0; j < d; j++) {
+          r.mat[2 * (i * d + j)] = g.mat[2 * (j * d + i)];
+          r.mat[2 * (i * d + j) + 1] = -g.mat[2 * (j * d + i) + 1];
+        }
+      break;
+    }
+    default: break;
+  }
+  return r;
+}
+
+// Gradient op (generator) of a parametrised gate and its factor f_gen.
+static LOp grad_op(const lq_gate& g, int n, double* fgen) {
+  LOp o;
+  o.type = OP_GRAD;
+  int b0 = n - 1 - g.qubits[0];
+  int b1 = gate_arity(g.kind) > 1 ? n - 1 - g.qubits[1] : 0;
+  uint64_t m0 = 1ull << b0, m1 = 1ull << b1;
+  int ny = 0;
+  *fgen = 1.0;
+  switch (g.kind) {
+    case LQ_RX: o.x = m0; break;
+    case LQ_RY: o.x = m0; o.z = m0; ny = 1; break;
+    case LQ_RZ: o.z = m0; break;
+    case LQ_RXX: o.x = m0 | m1; break;
+    case LQ_RYY: o.x = m0 | m1; o.z = m0 | m1; ny = 2; break;
+    case LQ_RZZ: o.z = m0 | m1; break;
+    case LQ_P: o.cm = o.cv = m0; *fgen = -2.0; break;
+    case LQ_CP: o.cm = o.cv = m0 | m1; *fgen = -2.0; break;
+    case LQ_CRX: o.cm = o.cv = m0; o.x = m1; break;
+    case LQ_CRY: o.cm = o.cv = m0; o.x = m1; o.z = m1; ny = 1; break;
+    case LQ_CRZ: o.cm = o.cv = m0; o.z = m1; break;
+    default: break;
+  }
+  o.mode = (uint8_t)(ny & 3);
+  return o;
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+extern "C" {
+
+size_t lq_adjoint_workspace_size(int n, int ng, int np, int nt) {
+  if (n < 1 || n > 34 || ng < 0 || np < 0) return 0;
+  int k = n < 10 ? n : 10;
+  int grid = pass2_grid(n, k);
+  std::size_t slots = (std::size_t)ng;   // at most one gradient op per gate
+  return 2 * align256(sizeof(double2) << n) + align256(sizeof(double) * slots * grid) +
+         align256(sizeof(double) * (slots + 1)) + 2 * align256(sizeof(int) * (np + 1)) +
+         align256(sizeof(double) * (np + 1)) + lq_expval_workspace_size(n, nt);
+}
+
+lq_status lq_adjoint_grad(int n, const lq_gate* gates, int ng, const double* params, int np,
+                          const lq_pauli_term* terms, int nt, double* energy, double* grad,
+                          void* workspace, size_t ws_bytes, lq_stream stream) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  st = check_gates(n, gates, ng, params, np);
+  if (st) return st;
+  st = check_terms(n, terms, nt);
+  if (st) return st;
+  if (!energy || (np > 0 && !grad)) return fail(LQ_ERR_INVALID_ARG, "NULL output");
+  std::size_t need = lq_adjoint_workspace_size(n, ng, np, nt);
+  if (!workspace || ws_bytes < need)
+    return fail(LQ_ERR_OOM, "workspace too small: %zu < %zu", ws_bytes, need);
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::size_t sb = sizeof(double2) << n;
+  ScheduleOptions opt;
+  const int k = opt.k < n ? opt.k : n;
+  const int grid = pass2_grid(n, k);
+
+  // workspace layout
+  char* p = (char*)workspace;
+  double2* psi = (double2*)p;
+  p += align256(sb);
+  double2* lam = (double2*)p;
+  p += align256(sb);
+  double* partial = (double*)p;
+  p += align256(sizeof(double) * (std::size_t)ng * grid);
+  double* d_factor = (double*)p;
+  p += align256(sizeof(double) * ((std::size_t)ng + 1));
+  int* d_first = (int*)p;
+  p += align256(sizeof(int) * (np + 1));
+  int* d_count = (int*)p;
+  p += align256(sizeof(int) * (np + 1));
+  double* d_out = (double*)p;   // [0] = E, [1..np] = grad
+  p += align256(sizeof(double) * (np + 1));
+  char* ews = p;
+  std::size_t ews_bytes = ws_bytes - (std::size_t)(p - (char*)workspace);
+
+  // forward: psi_L = U|0>, E = <H>, lambda = H psi_L
+  st = lq_state_init(psi, n, 0, stream);
+  if (st) return st;
+  st = lq_apply_circuit(psi, n, gates, ng, params, np, stream);
+  if (st) return st;
+  st = lq_expval_pauli_sum_async(psi, n, terms, nt, d_out, ews, ews_bytes, stream);
+  if (st) return st;
+  st = lq_apply_pauli_sum(lam, psi, n, terms, nt, stream);
+  if (st) return st;
+
+  // reverse sweep lowered into ops
+  std::vector<LOp> ops;
+  ops.reserve((std::size_t)ng * 2 + 8);
+  std::vector<double> factor;
+  std::vector<int> slot_param;
+  double zr = 1, zi = 0;
+  for (int gi = ng - 1; gi >= 0; gi--) {
+    const lq_gate& G = gates[gi];
+    double th = G.angle + (G.param >= 0 ? params[G.param] : 0.0);
+    if (G.param >= 0) {
+      double fgen;
+      LOp go = grad_op(G, n, &fgen);
+      go.slot = (int)factor.size();
+      go.gate = gi;
+      go.a = fgen;   // the |zeta|^2 part is added in execution order below
+      factor.push_back(fgen);
+      slot_param.push_back(G.param);
+      ops.push_back(go);
+    }
+    lq_gate inv = inverse_gate(G);
+    Lowered L;
+    st = lower_gate(inv, n, -th, L);
+    if (st) return st;
+    for (int j = 0; j < L.nops; j++) {
+      L.op[j].gate = gi;
+      if (j == 0) {
+        L.op[j].fr = L.zr;
+        L.op[j].fi = L.zi;
+      }
+      ops.push_back(L.op[j]);
+    }
+    double nr = zr * L.zr - zi * L.zi, ni = zr * L.zi + zi * L.zr;
+    zr = nr;
+    zi = ni;
+    double mag = std::hypot(zr, zi);
+    if (mag < 1e-100 || mag > 1e100) {
+      LOp sc;
+      sc.type = OP_SCALE;
+      sc.mode = 1;
+      sc.a = mag;
+      sc.fr = 1.0 / mag;
+      ops.push_back(sc);
+      zr /= mag;
+      zi /= mag;
+    }
+  }
+  const int nslots = (int)factor.size();
+  ScheduleOptions sopt;
+  Schedule S;
+  st = schedule_ops(n, ops.data(), ops.size(), zr, zi, sopt, S);
+  if (st) return st;
+  // A gradient op sees the states divided by the deferred scalar accumulated
+  // over the ops executed before it; the scheduler may reorder commuting
+  // ops, so accumulate in execution order.
+  {
+    double ar = 1, ai = 0;
+    for (int ps = 0; ps < S.npasses; ps++)
+      for (int o = 0; o < S.passes[ps].h.nops; o++) {
+        int src = S.op_src[ps * MAX_OPS + o];
+        if (src < 0) continue;
+        const LOp& l = ops[src];
+        if (l.type == OP_GRAD) {
+          factor[l.slot] = l.a * (ar * ar + ai * ai);
+        } else {
+          double nr2 = ar * l.fr - ai * l.fi, ni2 = ar * l.fi + ai * l.fr;
+          ar = nr2;
+          ai = ni2;
+        }
+      }
+  }
+  // slots grouped by parameter, in slot order
+  std::vector<int> first((std::size_t)np + 1, 0), count((std::size_t)np + 1, 0);
+  std::vector<int> order;
+  std::vector<double> fsorted;
+  for (int pi = 0; pi < np; pi++) {
+    first[pi] = (int)order.size();
+    for (int sl = 0; sl < nslots; sl++)
+      if (slot_param[sl] == pi) {
+        order.push_back(sl);
+        fsorted.push_back(factor[sl]);
+      }
+    count[pi] = (int)order.size() - first[pi];
+  }
+  // renumber slots so each parameter's slots are contiguous
+  std::vector<int> newslot((std::size_t)nslots + 1, 0);
+  for (std::size_t i = 0; i < order.size(); i++) newslot[order[i]] = (int)i;
+  // renumber the gradient ops inside the scheduled passes
+  for (int ps = 0; ps < S.npasses; ps++)
+    for (int o = 0; o < S.passes[ps].h.nops; o++)
+      if (S.passes[ps].ops[o].type == OP_GRAD)
+        S.passes[ps].ops[o].cidx = (uint32_t)newslot[S.passes[ps].ops[o].cidx];
+  if (nslots > 0) {
+    LQ_CUDA(cudaMemsetAsync(partial, 0, sizeof(double) * (std::size_t)nslots * grid, s));
+    LQ_CUDA(cudaMemcpyAsync(d_factor, fsorted.data(), sizeof(double) * nslots,
+                            cudaMemcpyHostToDevice, s));
+  }
+  if (np > 0) {
+    LQ_CUDA(cudaMemcpyAsync(d_first, first.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+    LQ_CUDA(cudaMemcpyAsync(d_count, count.data(), sizeof(int) * np, cudaMemcpyHostToDevice, s));
+  }
+  for (int ps = 0; ps < S.npasses; ps++) {
+    // the final scale would only rescale the uncomputed states: drop it
+    PassParams& P = S.passes[ps];
+    if (ps == S.npasses - 1 && P.h.nops > 0 && P.ops[P.h.nops - 1].type == OP_SCALE &&
+        (P.ops[P.h.nops - 1].mode & 2))
+      P.h.nops--;
+    if (P.h.nops == 0) continue;
+    LQ_CUDA(launch_pass2(P, psi, lam, partial, grid, s));
+  }
+  LQ_CUDA(launch_grad_reduce(partial, grid, d_factor, d_first, d_count, np, d_out + 1, s));
+  std::vector<double> h((std::size_t)np + 1);
+  LQ_CUDA(cudaMemcpyAsync(h.data(), d_out, sizeof(double) * (np + 1), cudaMemcpyDeviceToHost, s));
+  LQ_CUDA(cudaStreamSynchronize(s));
+  *energy = h[0];
+  for (int i = 0; i < np; i++) grad[i] = h[1 + i];
+  return LQ_OK;
+}
+
+}  // extern "C"

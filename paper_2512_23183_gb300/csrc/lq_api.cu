@@ -34,9 +34,11 @@ int sm_count() {
 #define LQ_CUDA(expr)                                                                  \
   do {                                                                                 \
     cudaError_t e_ = (expr);                                                           \
-    if (e_ != cudaSuccess)                                                             \
+    if (e_ != cudaSuccess) {                                                           \
+      (void)cudaGetLastError();                                                        \
       return fail(LQ_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
                   __LINE__);                                                           \
+    }                                                                                  \
   } while (0)
 
 static inline std::size_t align256(std::size_t b) { return (b + 255) & ~(std::size_t)255; }

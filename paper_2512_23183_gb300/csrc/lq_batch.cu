@@ -1,0 +1,599 @@
+// lq_batch.cu -- batched gradients in one persistent launch.
+//
+// The circuits of a parameter-shift gradient (Sec. III-A Eq. parameter_shift:
+// the base circuit and the +-s shifted copies per parameter, each run from
+// |0...0>, Sec. III-C) -- and, for uneven batches, the circuits of many
+// independent problems -- are work items of one persistent kernel.  Each
+// CTA takes the next circuit from an atomic work counter (items in
+// decreasing cost order, largest first), runs all of its tile passes on it,
+// evaluates <H>, and writes the energy; the last CTA to finish combines the
+// energies into gradients with the shift-rule weights.  No CTA waits on
+// another, so the launch has no inter-CTA spin-waits.
+//
+// A circuit whose state fits a tile (n <= 12) lives in shared memory from
+// |0...0> to <H> and never touches HBM; a larger one uses a per-CTA scratch
+// state in the workspace.  Circuits of one problem share one op program
+// lowered at the base angles; a circuit differs only in the coefficients of
+// its shifted gate and in the deferred scalar (a Patch).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lq_coefs.h"
+#include "lq_device.cuh"
+#include "lq_internal.h"
+#include "lq_kernels.h"
+
+namespace lq {
+
+#define LQ_CUDA(expr)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      (void)cudaGetLastError();                                                        \
+      return fail(LQ_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                           \
+    }                                                                                  \
+  } while (0)
+
+static inline std::size_t align256(std::size_t b) { return (b + 255) & ~(std::size_t)255; }
+
+constexpr int BATCH_SMEM_BITS = 12;   // whole-state tiles up to n = 12
+constexpr int BATCH_TILE_BITS = 10;   // tile width of larger states
+
+struct BPass {
+  PassHeader h;
+  int32_t op_first, coef_first;
+};
+
+struct BProb {
+  int32_t n, k, npasses, pass_first;
+  int32_t ngroups, group_first;
+  int32_t circ_first, ncirc;
+  int32_t np, out_first;
+  int32_t comb_first, pad;
+};
+
+struct BatchArgs {
+  const BProb* probs;
+  const BPass* passes;
+  const Op* ops;
+  const double* coef;
+  const ExpGroup* groups;
+  const ExpTerm* terms;
+  const Patch* patches;        // per circuit
+  const int32_t* circ_prob;    // per circuit
+  const int32_t* items;        // circuits in execution order
+  const int32_t* comb_first;   // per (problem, parameter): first combine entry
+  const int32_t* comb_count;
+  const int32_t* comb_circ;    // circuit offset within the problem
+  const double* comb_w;
+  double* E;                   // per circuit
+  double* out;                 // per problem: E, grad[np]
+  int32_t* counters;           // [0] next item, [1] finished CTAs
+  double2* scratch;            // per-CTA scratch states
+  uint64_t scratch_stride;     // amplitudes
+  int32_t nitems, nprobs;
+};
+
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0;
+  for (int w = 0; w < BLOCK / 32; w++) s += red[w];
+  return s;
+}
+
+// <H> of one state (shared or global memory) by one block: same grouping and
+// pair formula as expval_kernel.
+template <int BLOCK>
+__device__ double expval_block(const double2* st, int n, const ExpGroup* groups, int ngroups,
+                               const ExpTerm* terms, double* red) {
+  const uint64_t N = 1ull << n;
+  double acc = 0.0;
+  for (int g = 0; g < ngroups; g++) {
+    const ExpGroup G = groups[g];
+    if (G.x == 0) {
+      for (uint64_t i = threadIdx.x; i < N; i += BLOCK) {
+        const double2 v = st[i];
+        const double p = fma(v.x, v.x, v.y * v.y);
+        for (int t = G.first; t < G.first + G.count; t++) {
+          const uint32_t f = (uint32_t)(__popcll(i & terms[t].z) & 1) << 31;
+          acc = fma(xsign(terms[t].c, f), p, acc);
+        }
+      }
+    } else {
+      for (uint64_t j = threadIdx.x; j < (N >> 1); j += BLOCK) {
+        const uint64_t i = insert0_64(j, G.h), l = i ^ G.x;
+        const double2 a = st[i], b = st[l];
+        const double vr = fma(a.x, b.x, a.y * b.y);
+        const double vi = fma(a.x, b.y, -(a.y * b.x));
+        for (int t = G.first; t < G.first + G.count; t++) {
+          const int kk = (terms[t].k0 + 2 * (__popcll(l & terms[t].z) & 1)) & 3;
+          const double val = (kk & 1) ? vi : vr;
+          const uint32_t f = (uint32_t)(((kk + 1) & 2) >> 1) << 31;
+          acc = fma(xsign(terms[t].c2, f), val, acc);
+        }
+      }
+    }
+  }
+  return block_sum<BLOCK>(acc, red);
+}
+
+// The op with the circuit's patch applied (shifted gate coefficients, final
+// scale times the ratio of deferred factors).
+__device__ __forceinline__ Op patched(const Op& src, const Patch& pt) {
+  Op op = src;
+  if ((int)op.cidx == pt.gate &&
+      (op.type == OP_PAULI || op.type == OP_PHASE || op.type == OP_PARITY)) {
+    if (op.b1 == 0) {
+      op.a = pt.a0;
+      op.b = pt.b0;
+      if (op.type == OP_PAULI) op.mode = (uint8_t)((op.mode & ~3) | pt.mode0);
+    } else {
+      op.a = pt.a1;
+      op.b = pt.b1;
+    }
+  } else if (op.type == OP_SCALE && (op.mode & 2)) {
+    const double ar = op.a, ai = op.b;
+    op.a = ar * pt.zr - ai * pt.zi;
+    op.b = ar * pt.zi + ai * pt.zr;
+    op.mode &= ~1;
+  }
+  return op;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__ BatchArgs A) {
+  extern __shared__ double2 sm[];
+  __shared__ uint64_t hioff[256];
+  __shared__ double red[BLOCK / 32];
+  __shared__ int s_item, s_last;
+  double2* __restrict__ scratch = A.scratch + (uint64_t)blockIdx.x * A.scratch_stride;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&A.counters[0], 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= A.nitems) break;
+    const int c = A.items[it];
+    const BProb P = A.probs[A.circ_prob[c]];
+    const Patch pt = A.patches[c];
+    const int n = P.n;
+    double e;
+    if (n <= P.k) {
+      // whole state in shared memory
+      const uint32_t T = 1u << n;
+      for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+        sm[s] = make_double2(s == 0 ? 1.0 : 0.0, 0.0);
+      __syncthreads();
+      for (int p = 0; p < P.npasses; p++) {
+        const BPass& B = A.passes[P.pass_first + p];
+        for (int o = 0; o < B.h.nops; o++) {
+          const Op op = patched(A.ops[B.op_first + o], pt);
+          apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, 0);
+          __syncthreads();
+        }
+      }
+      e = expval_block<BLOCK>(sm, n, A.groups + P.group_first, P.ngroups, A.terms, red);
+    } else {
+      // tile passes over the CTA's scratch state
+      for (int p = 0; p < P.npasses; p++) {
+        const BPass& B = A.passes[P.pass_first + p];
+        const int k = B.h.k, m = B.h.m, kh = k - m;
+        const uint32_t T = 1u << k, lowmask = (1u << m) - 1u;
+        for (uint32_t j = threadIdx.x; j < (1u << kh); j += BLOCK)
+          hioff[j] = deposit(j, B.h.tbits + m, kh);
+        __syncthreads();
+        for (uint64_t t = 0; t < B.h.ntiles; t++) {
+          const uint64_t base = deposit(t, B.h.obits, B.h.nobits);
+          if (p == 0) {
+            for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+              sm[s] = make_double2((base == 0 && s == 0) ? 1.0 : 0.0, 0.0);
+          } else {
+            for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+              sm[s] = scratch[base | hioff[s >> m] | (s & lowmask)];
+          }
+          __syncthreads();
+          for (int o = 0; o < B.h.nops; o++) {
+            const Op op = patched(A.ops[B.op_first + o], pt);
+            apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, base);
+            __syncthreads();
+          }
+          for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+            scratch[base | hioff[s >> m] | (s & lowmask)] = sm[s];
+          __syncthreads();
+        }
+      }
+      e = expval_block<BLOCK>(scratch, n, A.groups + P.group_first, P.ngroups, A.terms, red);
+    }
+    if (threadIdx.x == 0) A.E[c] = e;
+  }
+  // the last CTA to finish combines energies into gradients
+  __threadfence();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&A.counters[1], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const volatile double* E = A.E;
+  for (int pi = 0; pi < A.nprobs; pi++) {
+    const BProb P = A.probs[pi];
+    if (threadIdx.x == 0) A.out[P.out_first] = E[P.circ_first];
+    for (int i = threadIdx.x; i < P.np; i += BLOCK) {
+      double g = 0;
+      const int f = A.comb_first[P.comb_first + i], cnt = A.comb_count[P.comb_first + i];
+      for (int q = f; q < f + cnt; q++) g += A.comb_w[q] * E[P.circ_first + A.comb_circ[q]];
+      A.out[P.out_first + 1 + i] = g;
+    }
+  }
+}
+
+// ---------------------------------------------------------- host side
+
+static const double kPi = 3.14159265358979323846;
+
+static bool two_term_kind(int kind) {
+  switch (kind) {
+    case LQ_RX: case LQ_RY: case LQ_RZ: case LQ_P: case LQ_CP: case LQ_RXX: case LQ_RYY:
+    case LQ_RZZ:
+      return true;
+    default:
+      return false;
+  }
+}
+
+static Patch patch_for(const lq_gate& G, int g, double theta_base, double theta) {
+  Patch p;
+  std::memset(&p, 0, sizeof p);
+  AngleCoefs a0, a1;
+  angle_coefs(G.kind, theta_base, a0);
+  angle_coefs(G.kind, theta, a1);
+  p.gate = g;
+  p.mode0 = a1.mode0;
+  p.mode1 = a1.mode1;
+  p.a0 = a1.a0;
+  p.b0 = a1.b0;
+  p.a1 = a1.a1;
+  p.b1 = a1.b1;
+  double den = a0.zr * a0.zr + a0.zi * a0.zi;
+  p.zr = (a1.zr * a0.zr + a1.zi * a0.zi) / den;
+  p.zi = (a1.zi * a0.zr - a1.zr * a0.zi) / den;
+  return p;
+}
+
+static Patch unpatched() {
+  Patch p;
+  std::memset(&p, 0, sizeof p);
+  p.gate = -2;
+  p.zr = 1.0;
+  return p;
+}
+
+// Build the circuits of a problem.  general = 0: two-term rule, every
+// parameter on at most one gate (else LQ_ERR_UNSUPPORTED); general = 1:
+// four-term rule for controlled rotations, shared parameters summed.
+lq_status make_problem(int n, const lq_gate* gates, int ng, const double* params, int np,
+                       const lq_pauli_term* terms, int nt, bool want_grad, bool general,
+                       HostProblem& hp) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  st = check_gates(n, gates, ng, params, np);
+  if (st) return st;
+  st = check_terms(n, terms, nt);
+  if (st) return st;
+  hp.n = n;
+  hp.ng = ng;
+  hp.np = np;
+  hp.nt = nt;
+  hp.gates = gates;
+  hp.params = params;
+  hp.terms = terms;
+  hp.patches.assign(1, unpatched());
+  hp.comb.assign((std::size_t)np, {});
+  if (!want_grad) return LQ_OK;
+  std::vector<int> uses((std::size_t)np, 0);
+  for (int g = 0; g < ng; g++) {
+    const lq_gate& G = gates[g];
+    if (G.param < 0) continue;
+    const bool two = two_term_kind(G.kind);
+    const bool four = G.kind == LQ_CRX || G.kind == LQ_CRY || G.kind == LQ_CRZ;
+    if (!general) {
+      if (!two)
+        return fail(LQ_ERR_UNSUPPORTED,
+                    "gate %d (kind %d) needs a generalised shift rule; use "
+                    "lq_param_shift_grad_general or lq_adjoint_grad", g, G.kind);
+      if (uses[G.param]++)
+        return fail(LQ_ERR_UNSUPPORTED,
+                    "parameter %d drives several gates; use lq_param_shift_grad_general",
+                    G.param);
+    }
+    double th = G.angle + params[G.param];
+    double sh[4], w[4];
+    int cnt = 0;
+    if (two) {
+      sh[0] = kPi / 2; w[0] = 0.5;
+      sh[1] = -kPi / 2; w[1] = -0.5;
+      cnt = 2;
+    } else if (four) {
+      const double r2 = std::sqrt(2.0);
+      const double d1 = (r2 + 1) / (4 * r2), d2 = (r2 - 1) / (4 * r2);
+      sh[0] = kPi / 2; w[0] = d1;
+      sh[1] = -kPi / 2; w[1] = -d1;
+      sh[2] = 3 * kPi / 2; w[2] = -d2;
+      sh[3] = -3 * kPi / 2; w[3] = d2;
+      cnt = 4;
+    }
+    for (int j = 0; j < cnt; j++) {
+      hp.comb[G.param].push_back({(int)hp.patches.size(), w[j]});
+      hp.patches.push_back(patch_for(G, g, th, th + sh[j]));
+    }
+  }
+  return LQ_OK;
+}
+
+// Device layout of a batch run, computed on the host.
+struct BatchPlan {
+  std::vector<BProb> probs;
+  std::vector<BPass> passes;
+  std::vector<Op> ops;
+  std::vector<double> coef;
+  std::vector<ExpGroup> groups;
+  std::vector<ExpTerm> terms;
+  std::vector<Patch> patches;
+  std::vector<int32_t> circ_prob, items, comb_first, comb_count, comb_circ;
+  std::vector<double> comb_w;
+  int kmax = 0, nmax_scratch = 0, nout = 0;
+  std::size_t program_bytes = 0;
+};
+
+static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B) {
+  std::vector<double> cost;
+  for (std::size_t pi = 0; pi < hps.size(); pi++) {
+    const HostProblem& hp = hps[pi];
+    const int n = hp.n;
+    LOp* ops = nullptr;
+    std::size_t nops = 0;
+    double zr, zi;
+    lq_status st = lower_circuit(n, hp.gates, hp.ng, hp.params, hp.np, &ops, &nops, &zr, &zi);
+    if (st) return st;
+    ScheduleOptions opt;
+    opt.k = n <= BATCH_SMEM_BITS ? n : BATCH_TILE_BITS;
+    opt.force_scale = true;
+    Schedule S;
+    st = schedule_ops(n, ops, nops, zr, zi, opt, S);
+    double flops = 0;
+    for (std::size_t i = 0; i < nops; i++) flops += op_flops(ops[i], n);
+    delete[] ops;
+    if (st) return st;
+    BProb P;
+    std::memset(&P, 0, sizeof P);
+    P.n = n;
+    P.k = opt.k < n ? opt.k : n;
+    P.npasses = S.npasses;
+    P.pass_first = (int)B.passes.size();
+    for (int p = 0; p < S.npasses; p++) {
+      BPass bp;
+      bp.h = S.passes[p].h;
+      bp.op_first = (int)B.ops.size();
+      bp.coef_first = (int)B.coef.size();
+      for (int o = 0; o < bp.h.nops; o++) B.ops.push_back(S.passes[p].ops[o]);
+      int ncoef = 0;
+      for (int o = 0; o < bp.h.nops; o++) {
+        const Op& d = S.passes[p].ops[o];
+        if (d.type == OP_PAIR_GEN) ncoef = std::max(ncoef, (int)d.cidx + 8);
+        if (d.type == OP_QUAD_GEN) ncoef = std::max(ncoef, (int)d.cidx + 32);
+      }
+      for (int c = 0; c < ncoef; c++) B.coef.push_back(S.passes[p].coef[c]);
+      B.passes.push_back(bp);
+    }
+    // Hamiltonian groups (absolute term indices)
+    int nch = exp_chunk_count(hp.terms, hp.nt);
+    std::vector<ExpParams> ch((std::size_t)nch);
+    int got = hp.nt ? build_exp_chunks(n, hp.terms, hp.nt, ch.data(), nch) : 0;
+    P.group_first = (int)B.groups.size();
+    for (int c = 0; c < got; c++) {
+      int tbase = (int)B.terms.size();
+      int used = 0;
+      for (int g = 0; g < ch[c].ngroups; g++) used += ch[c].groups[g].count;
+      for (int t = 0; t < used; t++) B.terms.push_back(ch[c].terms[t]);
+      for (int g = 0; g < ch[c].ngroups; g++) {
+        ExpGroup G = ch[c].groups[g];
+        G.first += tbase;
+        B.groups.push_back(G);
+      }
+    }
+    P.ngroups = (int)B.groups.size() - P.group_first;
+    P.circ_first = (int)B.patches.size();
+    P.ncirc = (int)hp.patches.size();
+    P.np = hp.np;
+    P.out_first = B.nout;
+    B.nout += 1 + hp.np;
+    P.comb_first = (int)B.comb_first.size();
+    for (int i = 0; i < hp.np; i++) {
+      B.comb_first.push_back((int)B.comb_circ.size());
+      B.comb_count.push_back((int)hp.comb[i].size());
+      for (auto& cw : hp.comb[i]) {
+        B.comb_circ.push_back(cw.first);
+        B.comb_w.push_back(cw.second);
+      }
+    }
+    double ecost = 0;
+    for (int t = 0; t < hp.nt; t++) ecost += 2.0;
+    double per = flops + (ecost + 6.0) * std::ldexp(1.0, n);
+    for (std::size_t c = 0; c < hp.patches.size(); c++) {
+      B.patches.push_back(hp.patches[c]);
+      B.circ_prob.push_back((int)pi);
+      cost.push_back(per);
+    }
+    B.kmax = std::max(B.kmax, P.k);
+    if (n > P.k) B.nmax_scratch = std::max(B.nmax_scratch, n);
+    B.probs.push_back(P);
+  }
+  // largest circuits first
+  B.items.resize(B.patches.size());
+  for (std::size_t i = 0; i < B.items.size(); i++) B.items[i] = (int)i;
+  std::stable_sort(B.items.begin(), B.items.end(),
+                   [&](int a, int b) { return cost[a] > cost[b]; });
+  return LQ_OK;
+}
+
+static int batch_grid(const BatchPlan& B) {
+  std::size_t smem = sizeof(double2) << B.kmax;
+  int per_sm = smem <= 16384 ? 6 : smem <= 32768 ? 4 : smem <= 65536 ? 3 : 1;
+  int g = sm_count() * per_sm;
+  if ((int)B.items.size() < g) g = (int)B.items.size();
+  if (B.nmax_scratch > 0) {
+    // keep the scratch states within 48 GiB
+    std::size_t sb = sizeof(double2) << B.nmax_scratch;
+    std::size_t cap = ((std::size_t)48 << 30) / sb;
+    if (cap < 1) cap = 1;
+    if ((std::size_t)g > cap) g = (int)cap;
+  }
+  return g < 1 ? 1 : g;
+}
+
+template <typename T>
+static std::size_t vbytes(const std::vector<T>& v) {
+  return align256(sizeof(T) * (v.size() > 0 ? v.size() : 1));
+}
+
+static std::size_t batch_bytes(const BatchPlan& B, int grid) {
+  std::size_t b = 0;
+  b += vbytes(B.probs) + vbytes(B.passes) + vbytes(B.ops) + vbytes(B.coef) + vbytes(B.groups) +
+       vbytes(B.terms) + vbytes(B.patches) + vbytes(B.circ_prob) + vbytes(B.items) +
+       vbytes(B.comb_first) + vbytes(B.comb_count) + vbytes(B.comb_circ) + vbytes(B.comb_w);
+  b += align256(sizeof(double) * B.patches.size());   // E
+  b += align256(sizeof(double) * (std::size_t)B.nout); // out
+  b += align256(sizeof(int32_t) * 2);                  // counters
+  if (B.nmax_scratch > 0) b += (sizeof(double2) << B.nmax_scratch) * (std::size_t)grid;
+  return b;
+}
+
+// Run the batch; results (per problem E then grad) into host vector `out`.
+static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_bytes,
+                           cudaStream_t s, std::vector<double>& out) {
+  const int grid = batch_grid(B);
+  if (!workspace || ws_bytes < batch_bytes(B, grid))
+    return fail(LQ_ERR_OOM, "workspace too small: %zu < %zu", ws_bytes, batch_bytes(B, grid));
+  char* p = (char*)workspace;
+  BatchArgs A;
+  std::memset(&A, 0, sizeof A);
+  std::vector<char> host;   // program image uploaded with one copy
+  std::size_t off = 0;
+  auto place = [&](const void* src, std::size_t n, std::size_t cap) {
+    std::size_t at = off;
+    host.resize(off + cap);
+    if (n) std::memcpy(host.data() + at, src, n);
+    off += cap;
+    return p + at;
+  };
+#define LQ_PLACE(vec, field, type) \
+  A.field = (type)place(vec.data(), sizeof(vec[0]) * vec.size(), vbytes(vec))
+  LQ_PLACE(B.probs, probs, const BProb*);
+  LQ_PLACE(B.passes, passes, const BPass*);
+  LQ_PLACE(B.ops, ops, const Op*);
+  LQ_PLACE(B.coef, coef, const double*);
+  LQ_PLACE(B.groups, groups, const ExpGroup*);
+  LQ_PLACE(B.terms, terms, const ExpTerm*);
+  LQ_PLACE(B.patches, patches, const Patch*);
+  LQ_PLACE(B.circ_prob, circ_prob, const int32_t*);
+  LQ_PLACE(B.items, items, const int32_t*);
+  LQ_PLACE(B.comb_first, comb_first, const int32_t*);
+  LQ_PLACE(B.comb_count, comb_count, const int32_t*);
+  LQ_PLACE(B.comb_circ, comb_circ, const int32_t*);
+  LQ_PLACE(B.comb_w, comb_w, const double*);
+#undef LQ_PLACE
+  const std::size_t image = off;
+  A.E = (double*)(p + off);
+  off += align256(sizeof(double) * B.patches.size());
+  A.out = (double*)(p + off);
+  off += align256(sizeof(double) * (std::size_t)B.nout);
+  A.counters = (int32_t*)(p + off);
+  off += align256(sizeof(int32_t) * 2);
+  A.scratch = (double2*)(p + off);
+  A.scratch_stride = B.nmax_scratch > 0 ? (1ull << B.nmax_scratch) : 0;
+  A.nitems = (int)B.items.size();
+  A.nprobs = (int)B.probs.size();
+  LQ_CUDA(cudaMemcpyAsync(p, host.data(), image, cudaMemcpyHostToDevice, s));
+  LQ_CUDA(cudaMemsetAsync(A.counters, 0, sizeof(int32_t) * 2, s));
+  static bool configured = false;
+  if (!configured) {
+    LQ_CUDA(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(double2) << BATCH_SMEM_BITS)));
+    configured = true;
+  }
+  batch_kernel<256><<<grid, 256, sizeof(double2) << B.kmax, s>>>(A);
+  LQ_CUDA(cudaGetLastError());
+  out.assign((std::size_t)B.nout, 0.0);
+  LQ_CUDA(cudaMemcpyAsync(out.data(), A.out, sizeof(double) * B.nout, cudaMemcpyDeviceToHost, s));
+  LQ_CUDA(cudaStreamSynchronize(s));
+  return LQ_OK;
+}
+
+std::size_t batch_workspace_for(const std::vector<HostProblem>& hps, lq_status* st_out) {
+  BatchPlan B;
+  lq_status st = plan_batch(hps, B);
+  if (st_out) *st_out = st;
+  if (st) return 0;
+  return batch_bytes(B, batch_grid(B));
+}
+
+lq_status batch_run(const std::vector<HostProblem>& hps, void* ws, std::size_t ws_bytes,
+                    cudaStream_t s, std::vector<double>& out) {
+  BatchPlan B;
+  lq_status st = plan_batch(hps, B);
+  if (st) return st;
+  return run_batch(B, ws, ws_bytes, s, out);
+}
+
+}  // namespace lq
+
+using namespace lq;
+
+extern "C" {
+
+size_t lq_batch_workspace_size(const lq_problem* problems, int count) {
+  if (!problems || count <= 0) return 0;
+  std::vector<HostProblem> hps((std::size_t)count);
+  for (int i = 0; i < count; i++) {
+    const lq_problem& q = problems[i];
+    if (make_problem(q.n, q.gates, q.ng, q.params, q.np, q.terms, q.nt, q.want_grad != 0, false,
+                     hps[i]))
+      return 0;
+  }
+  return batch_workspace_for(hps, nullptr);
+}
+
+lq_status lq_batch_param_shift(const lq_problem* problems, int count, void* workspace,
+                               size_t ws_bytes, lq_stream stream) {
+  if (!problems || count <= 0) return fail(LQ_ERR_INVALID_ARG, "no problems");
+  std::vector<HostProblem> hps((std::size_t)count);
+  for (int i = 0; i < count; i++) {
+    const lq_problem& q = problems[i];
+    if (!q.energy || (q.want_grad && q.np > 0 && !q.grad))
+      return fail(LQ_ERR_INVALID_ARG, "problem %d: NULL output", i);
+    lq_status st = make_problem(q.n, q.gates, q.ng, q.params, q.np, q.terms, q.nt,
+                                q.want_grad != 0, false, hps[i]);
+    if (st) return st;
+  }
+  std::vector<double> out;
+  lq_status st = batch_run(hps, workspace, ws_bytes, (cudaStream_t)stream, out);
+  if (st) return st;
+  std::size_t at = 0;
+  for (int i = 0; i < count; i++) {
+    const lq_problem& q = problems[i];
+    *q.energy = out[at];
+    if (q.want_grad)
+      for (int j = 0; j < q.np; j++) q.grad[j] = out[at + 1 + j];
+    at += 1 + q.np;
+  }
+  return LQ_OK;
+}
+
+}  // extern "C"

@@ -39,6 +39,19 @@ __device__ __forceinline__ uint64_t insert0_64(uint64_t j, int b) {
   return ((j ^ lo) << 1) | lo;
 }
 
+// Expand j into a tile index whose bits in mask M take the values of V and
+// whose other bits are the bits of j in order (so every lane of a loop over
+// j < T >> popcount(M) lands on an amplitude the op changes).
+__device__ __forceinline__ uint32_t expand(uint32_t j, uint32_t M, uint32_t V) {
+  uint32_t s = j;
+  while (M) {
+    const int b = __ffs(M) - 1;
+    M &= M - 1;
+    s = insert0(s, b) | (V & (1u << b));
+  }
+  return s;
+}
+
 // Scatter the low bits of v onto the bit positions pos[0..cnt).
 __device__ __forceinline__ uint64_t deposit(uint64_t v, const int8_t* pos, int cnt) {
   uint64_t r = 0;
@@ -61,10 +74,11 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       const int h = 31 - __clz(x);
       const int k0 = op.mode >> 2, pm = op.mode & 3;
       const double a = op.a, b = op.b;
-      for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
-        uint32_t s0 = insert0(j, h);
-        if ((s0 & cm) != cv) continue;
-        uint32_t s1 = s0 ^ x;
+      const uint32_t M = cm | (1u << h);
+      const uint32_t cnt = T >> __popc(M);
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s0 = expand(j, M, cv);
+        const uint32_t s1 = s0 ^ x;
         double2 A = sm[s0], B = sm[s1];
         int kA = (k0 + 2 * ((__popc(s1 & z) + zs) & 1)) & 3;
         int kB = (k0 + 2 * ((__popc(s0 & z) + zs) & 1)) & 3;
@@ -90,10 +104,11 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
     }
     case OP_H: {
       const int bb = op.b0;
-      for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
-        uint32_t s0 = insert0(j, bb);
-        if ((s0 & cm) != cv) continue;
-        uint32_t s1 = s0 | (1u << bb);
+      const uint32_t M = cm | (1u << bb);
+      const uint32_t cnt = T >> __popc(M);
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s0 = expand(j, M, cv);
+        const uint32_t s1 = s0 | (1u << bb);
         double2 A = sm[s0], B = sm[s1];
         sm[s0] = make_double2(A.x + B.x, A.y + B.y);
         sm[s1] = make_double2(A.x - B.x, A.y - B.y);
@@ -105,10 +120,11 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       const double* M = coef + op.cidx;
       const double m00r = M[0], m00i = M[1], m01r = M[2], m01i = M[3];
       const double m10r = M[4], m10i = M[5], m11r = M[6], m11i = M[7];
-      for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
-        uint32_t s0 = insert0(j, bb);
-        if ((s0 & cm) != cv) continue;
-        uint32_t s1 = s0 | (1u << bb);
+      const uint32_t MM = cm | (1u << bb);
+      const uint32_t cnt = T >> __popc(MM);
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s0 = expand(j, MM, cv);
+        const uint32_t s1 = s0 | (1u << bb);
         double2 A = sm[s0], B = sm[s1];
         double2 o0, o1;
         o0.x = fma(m00r, A.x, fma(-m00i, A.y, fma(m01r, B.x, -m01i * B.y)));
@@ -122,11 +138,11 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
     }
     case OP_QUAD_GEN: {
       const int hb = op.b0, lb = op.b1;
-      const int lo = hb < lb ? hb : lb, hi = hb < lb ? lb : hb;
       const double* M = coef + op.cidx;
-      for (uint32_t j = tid; j < (T >> 2); j += BLOCK) {
-        uint32_t s = insert0(insert0(j, lo), hi);
-        if ((s & cm) != cv) continue;
+      const uint32_t MM = cm | (1u << hb) | (1u << lb);
+      const uint32_t cnt = T >> __popc(MM);
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s = expand(j, MM, cv);
         uint32_t idx[4] = {s, s | (1u << lb), s | (1u << hb), s | (1u << hb) | (1u << lb)};
         double2 v[4];
 #pragma unroll
@@ -147,11 +163,11 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
     }
     case OP_SWAP: {
       const int b0 = op.b0, b1 = op.b1;
-      const int lo = b0 < b1 ? b0 : b1, hi = b0 < b1 ? b1 : b0;
-      for (uint32_t j = tid; j < (T >> 2); j += BLOCK) {
-        uint32_t s = insert0(insert0(j, lo), hi);
-        if ((s & cm) != cv) continue;
-        uint32_t sa = s | (1u << b0), sb = s | (1u << b1);
+      const uint32_t MM = cm | (1u << b0) | (1u << b1);
+      const uint32_t cnt = T >> __popc(MM);
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s = expand(j, MM, cv);
+        const uint32_t sa = s | (1u << b0), sb = s | (1u << b1);
         double2 A = sm[sa];
         sm[sa] = sm[sb];
         sm[sb] = A;
@@ -160,35 +176,52 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
     }
     case OP_PHASE: {
       const double wr = op.a, wi = op.b;
-      for (uint32_t s = tid; s < T; s += BLOCK) {
-        if ((s & cm) != cv) continue;
+      const uint32_t cnt = T >> __popc(cm);
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s = expand(j, cm, cv);
         sm[s] = cmul(sm[s], wr, wi);
       }
       break;
     }
     case OP_SIGN: {
-      for (uint32_t s = tid; s < T; s += BLOCK) {
-        if ((s & cm) != cv) continue;
-        double2 v = sm[s];
+      const uint32_t cnt = T >> __popc(cm);
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s = expand(j, cm, cv);
+        const double2 v = sm[s];
         sm[s] = make_double2(xsign(v.x, 0x80000000u), xsign(v.y, 0x80000000u));
       }
       break;
     }
     case OP_MULI: {
       const int kk = op.mode & 3;
-      for (uint32_t s = tid; s < T; s += BLOCK) {
-        if ((s & cm) != cv) continue;
+      const uint32_t cnt = T >> __popc(cm);
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s = expand(j, cm, cv);
         sm[s] = mul_ipow(sm[s], kk);
       }
       break;
     }
     case OP_PARITY: {
-      const uint32_t z = op.z_loc;
+      // amplitudes with odd popcount(idx & z): pick the top free bit hz of z
+      // and set it so the parity is odd
+      const uint32_t z = op.z_loc, zf = z & ~cm;
       const double wr = op.a, wi = op.b;
-      for (uint32_t s = tid; s < T; s += BLOCK) {
-        if (((__popc(s & z) + zs) & 1) == 0) continue;
-        if ((s & cm) != cv) continue;
-        sm[s] = cmul(sm[s], wr, wi);
+      if (zf == 0) {  // parity fixed by the condition and CTA bits
+        const uint32_t cnt = T >> __popc(cm);
+        for (uint32_t j = tid; j < cnt; j += BLOCK) {
+          const uint32_t s = expand(j, cm, cv);
+          if (((__popc(s & z) + zs) & 1) == 0) continue;
+          sm[s] = cmul(sm[s], wr, wi);
+        }
+      } else {
+        const int hz = 31 - __clz(zf);
+        const uint32_t M = cm | (1u << hz);
+        const uint32_t cnt = T >> __popc(M);
+        for (uint32_t j = tid; j < cnt; j += BLOCK) {
+          uint32_t s = expand(j, M, cv);
+          s |= (uint32_t)(((__popc(s & z) + zs) & 1) ^ 1) << hz;
+          sm[s] = cmul(sm[s], wr, wi);
+        }
       }
       break;
     }

@@ -122,6 +122,8 @@ struct LOp {
   int gate = -1;                 // source gate index (-1: synthetic)
   int sub = 0;                   // index of this op among its gate's ops
   int slot = -1;                 // gradient slot (OP_GRAD)
+  double fr = 1, fi = 0;         // deferred factor this op contributes to the
+                                 // global scalar (first op of a gate)
   uint64_t mix() const;          // bits that must lie inside the tile
   uint64_t diag() const;         // bits only read (conditions, phases)
 };

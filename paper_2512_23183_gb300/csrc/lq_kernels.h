@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
+#include <vector>
 
 #include "lq_internal.h"
 
@@ -47,6 +49,29 @@ lq_status expval_states(const double2* states, uint64_t stride, int nstates, int
                         const lq_pauli_term* terms, int nt, double* partial, double* out_dev,
                         cudaStream_t s);
 
+// ------------------------------------------------- persistent batch runner
+
+// One problem as the batch runner sees it: circuit, Hamiltonian, the patch
+// of every circuit (index 0 = unshifted), and per parameter the (circuit,
+// weight) pairs of its shift rule.
+struct HostProblem {
+  int n = 0, ng = 0, np = 0, nt = 0;
+  const lq_gate* gates = nullptr;
+  const double* params = nullptr;
+  const lq_pauli_term* terms = nullptr;
+  std::vector<Patch> patches;
+  std::vector<std::vector<std::pair<int, double>>> comb;
+};
+
+lq_status make_problem(int n, const lq_gate* gates, int ng, const double* params, int np,
+                       const lq_pauli_term* terms, int nt, bool want_grad, bool general,
+                       HostProblem& hp);
+std::size_t batch_workspace_for(const std::vector<HostProblem>& hps, lq_status* st);
+// Runs every circuit of every problem in one persistent launch; out holds
+// per problem E then its np gradient entries.
+lq_status batch_run(const std::vector<HostProblem>& hps, void* ws, std::size_t ws_bytes,
+                    cudaStream_t s, std::vector<double>& out);
+
 // --------------------------------------------------------------- launchers
 
 int sm_count();
@@ -55,6 +80,12 @@ int expval_grid(int n);
 cudaError_t launch_init_basis(double2* amps, int n, uint64_t basis, cudaStream_t s);
 cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, int nstates,
                         cudaStream_t s, const Patch* patches = nullptr);
+int pass2_grid(int n, int k);
+cudaError_t launch_pass2(const PassParams& P, double2* psi, double2* lam, double* partial,
+                         int grid, cudaStream_t s);
+cudaError_t launch_grad_reduce(const double* partial, int grid, const double* factor,
+                               const int* first, const int* count, int np, double* grad,
+                               cudaStream_t s);
 cudaError_t launch_psr_grad(const double* E, int np, double* out, cudaStream_t s);
 cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, double scale,
                             cudaStream_t s);

@@ -27,9 +27,11 @@ namespace lq {
 #define LQ_CUDA(expr)                                                                  \
   do {                                                                                 \
     cudaError_t e_ = (expr);                                                           \
-    if (e_ != cudaSuccess)                                                             \
+    if (e_ != cudaSuccess) {                                                           \
+      (void)cudaGetLastError();                                                        \
       return fail(LQ_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
                   __LINE__);                                                           \
+    }                                                                                  \
   } while (0)
 
 static inline std::size_t align256(std::size_t b) { return (b + 255) & ~(std::size_t)255; }
@@ -72,105 +74,10 @@ __global__ void psr_grad_kernel(const double* __restrict__ E, int np, double* __
 }
 
 cudaError_t launch_psr_grad(const double* E, int np, double* out, cudaStream_t s) {
+  (void)cudaGetLastError();  // report only this launcher's own errors
   int n = np > 0 ? np : 1;
   psr_grad_kernel<<<(n + 127) / 128, 128, 0, s>>>(E, np, out);
   return cudaGetLastError();
-}
-
-// Patch of circuit (gate g shifted to angle theta): new op coefficients and
-// the ratio new/old of the gate's deferred factor.
-static Patch make_patch(const lq_gate& G, int g, double theta_base, double theta) {
-  Patch p;
-  std::memset(&p, 0, sizeof p);
-  AngleCoefs a0, a1;
-  angle_coefs(G.kind, theta_base, a0);
-  angle_coefs(G.kind, theta, a1);
-  p.gate = g;
-  p.mode0 = a1.mode0;
-  p.mode1 = a1.mode1;
-  p.a0 = a1.a0;
-  p.b0 = a1.b0;
-  p.a1 = a1.a1;
-  p.b1 = a1.b1;
-  // (a1.z) / (a0.z)
-  double den = a0.zr * a0.zr + a0.zi * a0.zi;
-  p.zr = (a1.zr * a0.zr + a1.zi * a0.zi) / den;
-  p.zi = (a1.zi * a0.zr - a1.zr * a0.zi) / den;
-  return p;
-}
-
-static Patch no_patch() {
-  Patch p;
-  std::memset(&p, 0, sizeof p);
-  p.gate = -2;
-  p.zr = 1.0;
-  return p;
-}
-
-// Expectation workspace layout helper (partials for `nstates`).
-static std::size_t exp_partials(int n, int nstates) {
-  return align256(sizeof(double) * (std::size_t)expval_grid(n) * (std::size_t)nstates);
-}
-
-// How many circuits the batched method runs per launch.
-static int psr_chunk(int n, int C) {
-  std::size_t sb = sizeof(double2) << n;
-  std::size_t cap = ((std::size_t)4 << 30) / sb;  // about 4 GiB of states per chunk
-  if (cap < 1) cap = 1;
-  return (int)((std::size_t)C < cap ? (std::size_t)C : cap);
-}
-
-static std::size_t batched_ws(int n, int C, int np) {
-  int chunk = psr_chunk(n, C);
-  return align256((sizeof(double2) << n) * (std::size_t)chunk) +
-         align256(sizeof(Patch) * (std::size_t)chunk) + exp_partials(n, chunk) +
-         align256(sizeof(double) * (std::size_t)C) + align256(sizeof(double) * (np + 1));
-}
-
-// Energies of C circuits that share the lowered schedule of (gates at
-// params), each modified by patches[c].  Writes E[0..C) (device).
-lq_status run_patched_energies(int n, const lq_gate* gates, int ng, const double* params,
-                               int np, const lq_pauli_term* terms, int nt,
-                               const std::vector<Patch>& patches, double* E_dev,
-                               char* ws, std::size_t ws_bytes, cudaStream_t s) {
-  const int C = (int)patches.size();
-  LOp* ops = nullptr;
-  std::size_t nops = 0;
-  double zr, zi;
-  lq_status st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi);
-  if (st) return st;
-  ScheduleOptions opt;
-  opt.force_scale = true;
-  Schedule S;
-  st = schedule_ops(n, ops, nops, zr, zi, opt, S);
-  delete[] ops;
-  if (st) return st;
-  const int chunk = psr_chunk(n, C);
-  const std::size_t sb = sizeof(double2) << n;
-  char* p = ws;
-  double2* states = (double2*)p;
-  p += align256(sb * (std::size_t)chunk);
-  Patch* d_patch = (Patch*)p;
-  p += align256(sizeof(Patch) * (std::size_t)chunk);
-  double* partial = (double*)p;
-  p += exp_partials(n, chunk);
-  if ((std::size_t)(p - ws) > ws_bytes) return fail(LQ_ERR_OOM, "workspace too small");
-  for (int c0 = 0; c0 < C; c0 += chunk) {
-    int cnt = C - c0 < chunk ? C - c0 : chunk;
-    LQ_CUDA(cudaMemcpyAsync(d_patch, patches.data() + c0, sizeof(Patch) * cnt,
-                            cudaMemcpyHostToDevice, s));
-    for (int ps = 0; ps < S.npasses; ps++) {
-      PassParams& P = S.passes[ps];
-      if (ps == 0) P.h.flags |= PF_INIT_ZERO;
-      LQ_CUDA(launch_pass(P, states, (uint64_t)1 << n, cnt, s, d_patch));
-    }
-    // expectation of every state of the chunk
-    st = expval_states(states, (uint64_t)1 << n, cnt, n, terms, nt, partial, E_dev + c0, s);
-    if (st) return st;
-    // the chunk's passes must finish before the patches buffer is reused
-    if (c0 + chunk < C) LQ_CUDA(cudaStreamSynchronize(s));
-  }
-  return LQ_OK;
 }
 
 }  // namespace lq
@@ -180,11 +87,31 @@ using namespace lq;
 extern "C" {
 
 size_t lq_param_shift_workspace_size(int n, int np, int nt, int method) {
-  (void)nt;
   if (n < 1 || n > 34 || np < 0) return 0;
   if (method == LQ_PSR_PLAIN)
     return align256(sizeof(double2) << n) + lq_expval_workspace_size(n, nt);
-  return batched_ws(n, 2 * np + 1, np);
+  // an HEA-shaped stand-in with np single-use rotations sizes the batch: the
+  // workspace depends on n, the number of circuits and the program size
+  std::vector<lq_gate> g((std::size_t)np);
+  std::vector<double> p((std::size_t)np, 0.0);
+  std::vector<lq_pauli_term> t((std::size_t)(nt > 0 ? nt : 0));
+  for (int i = 0; i < np; i++) {
+    std::memset(&g[i], 0, sizeof(lq_gate));
+    g[i].kind = LQ_RY;
+    g[i].qubits[0] = i % n;
+    g[i].qubits[1] = g[i].qubits[2] = -1;
+    g[i].param = i;
+  }
+  for (int i = 0; i < nt; i++) {
+    t[i].coeff = 1.0;
+    t[i].xmask = (uint64_t)(i % n);
+    t[i].zmask = 0;
+  }
+  HostProblem hp;
+  if (make_problem(n, g.data(), np, p.data(), np, t.data(), nt, true, false, hp)) return 0;
+  std::vector<HostProblem> v(1, hp);
+  // room for larger op programs than the stand-in: 1 MiB
+  return batch_workspace_for(v, nullptr) + ((std::size_t)1 << 20);
 }
 
 lq_status lq_param_shift_grad(int n, const lq_gate* gates, int ng, const double* params,
@@ -237,35 +164,16 @@ lq_status lq_param_shift_grad(int n, const lq_gate* gates, int ng, const double*
     return LQ_OK;
   }
 
-  // batched
-  const int C = 2 * np + 1;
-  std::vector<Patch> patches((std::size_t)C);
-  patches[0] = no_patch();
-  for (int i = 0; i < np; i++) {
-    int g = pg[i];
-    if (g < 0) {
-      patches[1 + 2 * i] = no_patch();
-      patches[2 + 2 * i] = no_patch();
-      continue;
-    }
-    double th = gates[g].angle + params[i];
-    patches[1 + 2 * i] = make_patch(gates[g], g, th, th + kPi / 2);
-    patches[2 + 2 * i] = make_patch(gates[g], g, th, th - kPi / 2);
-  }
-  char* ws = (char*)workspace;
-  const int chunk = psr_chunk(n, C);
-  std::size_t off = align256((sizeof(double2) << n) * (std::size_t)chunk) +
-                    align256(sizeof(Patch) * (std::size_t)chunk) + exp_partials(n, chunk);
-  double* E = (double*)(ws + off);
-  double* out = (double*)(ws + off + align256(sizeof(double) * (std::size_t)C));
-  st = run_patched_energies(n, gates, ng, params, np, terms, nt, patches, E, ws, off, s);
+  // batched: every circuit in one persistent launch
+  HostProblem hp;
+  st = make_problem(n, gates, ng, params, np, terms, nt, true, false, hp);
   if (st) return st;
-  LQ_CUDA(launch_psr_grad(E, np, out, s));
-  std::vector<double> h((std::size_t)np + 1);
-  LQ_CUDA(cudaMemcpyAsync(h.data(), out, sizeof(double) * (np + 1), cudaMemcpyDeviceToHost, s));
-  LQ_CUDA(cudaStreamSynchronize(s));
-  *energy = h[0];
-  for (int i = 0; i < np; i++) grad[i] = h[1 + i];
+  std::vector<HostProblem> v(1, hp);
+  std::vector<double> out;
+  st = batch_run(v, workspace, ws_bytes, s, out);
+  if (st) return st;
+  *energy = out[0];
+  for (int i = 0; i < np; i++) grad[i] = out[1 + i];
   return LQ_OK;
 }
 
@@ -352,8 +260,19 @@ lq_status lq_trotter_evolve(void* amps, int n, const lq_pauli_term* terms, int n
 
 size_t lq_param_shift_general_workspace_size(int n, const lq_gate* gates, int ng, int np,
                                              int nt) {
-  (void)n; (void)gates; (void)ng; (void)np; (void)nt;
-  return 256;
+  if (n < 1 || n > 34 || np < 0 || ng < 0 || (ng > 0 && !gates)) return 0;
+  // sizes depend on the circuit's structure only: evaluate at zero parameters
+  std::vector<double> p((std::size_t)(np > 0 ? np : 1), 0.0);
+  std::vector<lq_pauli_term> t((std::size_t)(nt > 0 ? nt : 1));
+  for (int i = 0; i < nt; i++) {
+    t[i].coeff = 1.0;
+    t[i].xmask = (uint64_t)(i % n);
+    t[i].zmask = 0;
+  }
+  HostProblem hp;
+  if (make_problem(n, gates, ng, p.data(), np, t.data(), nt, true, true, hp)) return 0;
+  std::vector<HostProblem> v(1, hp);
+  return batch_workspace_for(v, nullptr) + ((std::size_t)1 << 20);
 }
 
 lq_status lq_param_shift_grad_general(int n, const lq_gate* gates, int ng,
@@ -361,33 +280,17 @@ lq_status lq_param_shift_grad_general(int n, const lq_gate* gates, int ng,
                                       const lq_pauli_term* terms, int nt, double* energy,
                                       double* grad, void* workspace, size_t ws_bytes,
                                       lq_stream stream) {
-  (void)n; (void)gates; (void)ng; (void)params; (void)np; (void)terms; (void)nt;
-  (void)energy; (void)grad; (void)workspace; (void)ws_bytes; (void)stream;
-  return fail(LQ_ERR_UNSUPPORTED, "not built yet");
-}
-
-size_t lq_adjoint_workspace_size(int n, int ng, int np, int nt) {
-  (void)n; (void)ng; (void)np; (void)nt;
-  return 256;
-}
-
-lq_status lq_adjoint_grad(int n, const lq_gate* gates, int ng, const double* params, int np,
-                          const lq_pauli_term* terms, int nt, double* energy, double* grad,
-                          void* workspace, size_t ws_bytes, lq_stream stream) {
-  (void)n; (void)gates; (void)ng; (void)params; (void)np; (void)terms; (void)nt;
-  (void)energy; (void)grad; (void)workspace; (void)ws_bytes; (void)stream;
-  return fail(LQ_ERR_UNSUPPORTED, "not built yet");
-}
-
-size_t lq_batch_workspace_size(const lq_problem* problems, int count) {
-  (void)problems; (void)count;
-  return 256;
-}
-
-lq_status lq_batch_param_shift(const lq_problem* problems, int count, void* workspace,
-                               size_t ws_bytes, lq_stream stream) {
-  (void)problems; (void)count; (void)workspace; (void)ws_bytes; (void)stream;
-  return fail(LQ_ERR_UNSUPPORTED, "not built yet");
+  if (!energy || (np > 0 && !grad)) return fail(LQ_ERR_INVALID_ARG, "NULL output");
+  HostProblem hp;
+  lq_status st = make_problem(n, gates, ng, params, np, terms, nt, true, true, hp);
+  if (st) return st;
+  std::vector<HostProblem> v(1, hp);
+  std::vector<double> out;
+  st = batch_run(v, workspace, ws_bytes, (cudaStream_t)stream, out);
+  if (st) return st;
+  *energy = out[0];
+  for (int i = 0; i < np; i++) grad[i] = out[1 + i];
+  return LQ_OK;
 }
 
 }  // extern "C"

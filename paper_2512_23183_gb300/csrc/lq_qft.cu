@@ -52,6 +52,7 @@ __global__ void fft_table_kernel() {
 }
 
 cudaError_t fft_tables_init(cudaStream_t s) {
+  (void)cudaGetLastError();  // report only this launcher's own errors
   static int done_dev[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -162,6 +163,7 @@ static constexpr int kFftBlock = 256;
 
 cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, double scale,
                             cudaStream_t s) {
+  (void)cudaGetLastError();  // report only this launcher's own errors
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<kFftBlock>,
@@ -237,6 +239,7 @@ __global__ void bitrev_small_kernel(double2* __restrict__ state, int n) {
 }
 
 cudaError_t launch_bitrev(double2* state, int n, cudaStream_t s) {
+  (void)cudaGetLastError();  // report only this launcher's own errors
   if (n <= 12) {
     static bool conf = false;
     if (!conf) {
