@@ -161,6 +161,24 @@ lq_status lq_expval_pauli_sum_async(const void* amps, int n, const lq_pauli_term
                                     int nt, double* out_dev, void* workspace,
                                     size_t ws_bytes, lq_stream stream);
 
+/* Allocation-free <H>.  The paper has no counterpart to this entry point.
+ * It computes the same E as lq_expval_pauli_sum for callers that cannot
+ * allocate device memory -- code embedded in a host application whose device
+ * memory belongs to an allocator it cannot call, or a plugin that is handed
+ * only a state pointer -- so it needs no workspace: its partial sums live in
+ * one fixed array inside the library (4096 doubles = 32 KiB), which every GPU
+ * that loads the library holds until the process exits.  Limits: at most 640
+ * terms with at most 240 distinct X masks; larger sums return
+ * LQ_ERR_INVALID_ARG with a message (use lq_expval_pauli_sum then).  The
+ * first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, so calls whose work overlaps on the GPU (several streams or
+ * threads at once) race: serialise them.  No cudaMalloc, cudaFree or other
+ * allocating call is made.  out: host double; the call synchronises
+ * `stream`. */
+lq_status lq_expval_pauli_sum_noalloc(const void* amps, int n, const lq_pauli_term* terms,
+                                      int nt, double* out, lq_stream stream);
+
 /* out = H psi for H = sum_t c_t P_t (device buffers, out != in). */
 lq_status lq_apply_pauli_sum(void* out, const void* in, int n, const lq_pauli_term* terms,
                              int nt, lq_stream stream);

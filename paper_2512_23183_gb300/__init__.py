@@ -71,6 +71,7 @@ EXPORTS = [
     "lq_param_shift_general_workspace_size", "lq_param_shift_grad_general",
     "lq_adjoint_workspace_size", "lq_adjoint_grad", "lq_trotter_evolve",
     "lq_batch_workspace_size", "lq_batch_param_shift", "lq_circuit_plan", "lq_qft_plan",
+    "lq_expval_pauli_sum_noalloc",
 ]
 
 
