@@ -428,6 +428,56 @@ def vqe_extras(device):
     return res
 
 
+def serve_extras(device, count=48, slots=8):
+    """Serving workload: seeded request stream (n ~ U{8..28}, depth ~
+    U{2..20}, 50/50 energy / energy+gradient, Heisenberg chain or random
+    50-term sums), admitted by footprint against a device arena of up to
+    150 GB.  A closed-loop pass measures capacity; then the same requests
+    arrive as a Poisson stream at 70% of it.  Reports throughput and p50/p99
+    latency (submit -> done)."""
+    import numpy as np
+    import torch
+
+    import paper_2512_23183_gb300 as lq
+    import workloads as W
+
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(150e9, free - 8e9))
+    arena = torch.empty(budget, dtype=torch.uint8, device=device)
+    reqs = W.serve_requests(count, seed=6)
+    srv = lq.Server(arena, slots=slots)
+    try:
+        t0 = time.perf_counter()
+        ids = [srv.submit(r["n"], r["gates"], r["params"], r["terms"], r["grad"]) for r in reqs]
+        for i in ids:
+            srv.result(i)
+        cap = count / (time.perf_counter() - t0)
+        rate = 0.7 * cap
+        gaps = np.random.default_rng(6).exponential(1.0 / rate, count)
+        arrivals = np.cumsum(gaps)
+        start = time.perf_counter()
+        ids = []
+        for r, ta in zip(reqs, arrivals):
+            dt = start + ta - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(srv.submit(r["n"], r["gates"], r["params"], r["terms"], r["grad"]))
+        res = [srv.result(i) for i in ids]
+        end = max(t[2] for _, _, t in res)
+        first = min(t[0] for _, _, t in res)
+        lat = np.array([t[2] - t[0] for _, _, t in res])
+    finally:
+        srv.close()
+        del arena
+    return {"requests": count, "slots": slots, "arena_gb": round(budget / 1e9, 1),
+            "closed_loop_req_per_s": round(cap, 3), "poisson_rate_req_per_s": round(rate, 3),
+            "throughput_req_per_s": round(count / (end - first), 3),
+            "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
+            "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
+            "workload": "seed 6: n~U{8..28}, depth~U{2..20}, 50/50 energy/grad (adjoint), "
+                        "Heisenberg chain or random 50-term"}
+
+
 # ----------------------------------------------------------- CPU baseline
 
 def oracle_sample_rate(n):
@@ -514,6 +564,8 @@ def main():
     if rank == 0:
         if not a.no_extras:
             out["vqe"] = vqe_extras(device)
+            torch.cuda.empty_cache()
+            out["serve"] = serve_extras(device)
         out["cpu_baseline"] = cpu_baseline(a.cpu_n)
         print(json.dumps(out), flush=True)
     if world > 1:

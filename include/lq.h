@@ -284,6 +284,57 @@ size_t lq_batch_workspace_size(const lq_problem* problems, int count);
 lq_status lq_batch_param_shift(const lq_problem* problems, int count, void* workspace,
                                size_t ws_bytes, lq_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching request server (spec addition; the
+ * paper has no serving layer).  Requests carry one circuit, its parameters
+ * and a Pauli sum, energy only or energy and gradient (adjoint).  The server
+ * admits a request when its footprint (lq_server_footprint) fits in the free
+ * part of the caller's device arena and a worker slot is free; work of
+ * different requests overlaps on the device (one stream per slot), and
+ * small energy-only requests waiting together run in one batched launch.
+ * Gates, parameters and terms are copied at submit.  A result does not
+ * depend on what else is in flight.
+ */
+typedef struct lq_server lq_server;
+
+typedef struct {
+  int32_t n, ng, np, nt;
+  int32_t want_grad;            /* 0: energy only; 1: energy and gradient */
+  int32_t reserved;
+  const lq_gate* gates;         /* host, copied */
+  const double* params;         /* host, copied */
+  const lq_pauli_term* terms;   /* host, copied */
+} lq_request;
+
+typedef struct {
+  int64_t id;
+  int32_t status;               /* lq_status of the request */
+  int32_t np;
+  double energy;
+  double t_submit, t_start, t_done;   /* seconds, one monotonic clock */
+} lq_result;
+
+/* Device bytes one request occupies in the arena while it runs. */
+size_t lq_server_footprint(int n, int want_grad, int ng, int np, int nt);
+
+/* Create a server over the caller's device arena (current device) with
+ * `slots` concurrent workers.  The arena stays owned by the caller and must
+ * outlive the server. */
+lq_status lq_server_create(void* arena, size_t arena_bytes, int slots, lq_server** out);
+
+/* Queue a request; *id identifies it.  LQ_ERR_OOM if it can never fit. */
+lq_status lq_server_submit(lq_server* server, const lq_request* req, int64_t* id);
+
+/* Wait up to timeout_s seconds for request `id`; fills `res` and, for a
+ * gradient request, grad[0..np).  LQ_ERR_TIMEOUT if not done in time (the
+ * request stays queued).  A finished request is forgotten after this call. */
+lq_status lq_server_wait(lq_server* server, int64_t id, double timeout_s, lq_result* res,
+                         double* grad);
+
+/* Stop the workers (after the running requests finish) and free the server;
+ * requests still queued are dropped. */
+lq_status lq_server_destroy(lq_server* server);
+
 #ifdef __cplusplus
 }
 #endif

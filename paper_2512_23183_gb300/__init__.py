@@ -46,6 +46,19 @@ class LqProblem(ctypes.Structure):
                 ("grad", ctypes.POINTER(c_double))]
 
 
+class LqRequest(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("ng", c_int32), ("np", c_int32), ("nt", c_int32),
+                ("want_grad", c_int32), ("reserved", c_int32),
+                ("gates", ctypes.POINTER(LqGate)), ("params", ctypes.POINTER(c_double)),
+                ("terms", ctypes.POINTER(LqPauliTerm))]
+
+
+class LqResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", c_int32), ("np", c_int32),
+                ("energy", c_double), ("t_submit", c_double), ("t_start", c_double),
+                ("t_done", c_double)]
+
+
 # lq_gate_kind values of include/lq.h
 KINDS = {name: i for i, name in enumerate(
     "H X Y Z S SDG T TDG RX RY RZ P U1 CNOT CY CZ CP SWAP CRX CRY CRZ RXX RYY RZZ CCX U2".split())}
@@ -71,7 +84,8 @@ EXPORTS = [
     "lq_param_shift_general_workspace_size", "lq_param_shift_grad_general",
     "lq_adjoint_workspace_size", "lq_adjoint_grad", "lq_trotter_evolve",
     "lq_batch_workspace_size", "lq_batch_param_shift", "lq_circuit_plan", "lq_qft_plan",
-    "lq_expval_pauli_sum_noalloc",
+    "lq_expval_pauli_sum_noalloc", "lq_server_footprint", "lq_server_create",
+    "lq_server_submit", "lq_server_wait", "lq_server_destroy",
 ]
 
 
@@ -125,6 +139,12 @@ def load(build_if_missing=True):
     L.lq_batch_workspace_size.argtypes = [P(LqProblem), ctypes.c_int]
     L.lq_batch_workspace_size.restype = c_size_t
     L.lq_batch_param_shift.argtypes = [P(LqProblem), ctypes.c_int, c_void_p, c_size_t, c_void_p]
+    L.lq_server_footprint.argtypes = [ctypes.c_int] * 5
+    L.lq_server_footprint.restype = c_size_t
+    L.lq_server_create.argtypes = [c_void_p, c_size_t, ctypes.c_int, P(c_void_p)]
+    L.lq_server_submit.argtypes = [c_void_p, P(LqRequest), P(ctypes.c_int64)]
+    L.lq_server_wait.argtypes = [c_void_p, ctypes.c_int64, c_double, P(LqResult), P(c_double)]
+    L.lq_server_destroy.argtypes = [c_void_p]
     L.lq_circuit_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
                                   P(LqPlanInfo)]
     L.lq_qft_plan.argtypes = [ctypes.c_int, ctypes.c_int, P(LqPlanInfo)]
@@ -369,6 +389,53 @@ def batch_param_shift(problems, device="cuda", stream=None, workspace=None):
         pb.energy = float(e[0])
         pb.grad = gr[: pb.params.size].copy()
     return problems
+
+
+class Server:
+    """Continuous-batching request server over a device arena (a torch uint8
+    CUDA tensor the caller keeps alive).  submit() queues a request and
+    returns its id; result(id) waits and returns (energy, grad or None,
+    (t_submit, t_start, t_done))."""
+
+    def __init__(self, arena, slots=4):
+        self.arena = arena
+        h = c_void_p()
+        _check(load().lq_server_create(_ptr(arena), arena.numel(), int(slots), ctypes.byref(h)))
+        self.h = h
+        self._np = {}
+
+    def submit(self, n, gates, params, terms, want_grad=False):
+        L = load()
+        g = pack_gates(gates)
+        t = pack_terms(terms, n)
+        p = np.ascontiguousarray(np.asarray(params, np.float64))
+        q = LqRequest(n, len(gates), p.size, len(terms), int(want_grad), 0, g,
+                      p.ctypes.data_as(ctypes.POINTER(c_double)), t)
+        rid = ctypes.c_int64()
+        _check(L.lq_server_submit(self.h, ctypes.byref(q), ctypes.byref(rid)))
+        self._np[rid.value] = (p.size, want_grad)
+        return rid.value
+
+    def result(self, rid, timeout=600.0):
+        np_, want_grad = self._np.pop(rid)
+        res = LqResult()
+        grad = np.zeros(max(np_, 1))
+        _check(load().lq_server_wait(self.h, rid, float(timeout), ctypes.byref(res),
+                                     grad.ctypes.data_as(ctypes.POINTER(c_double))))
+        return res.energy, (grad[:np_].copy() if want_grad else None), (res.t_submit, res.t_start,
+                                                                       res.t_done)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lq_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def server_footprint(n, want_grad, ng, np_, nt):
+    return load().lq_server_footprint(n, int(want_grad), ng, np_, nt)
 
 
 from .autograd import AdjointEnergy, energy  # noqa: E402,F401

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
         const BPass& B = A.passes[P.pass_first + p];
         for (int o = 0; o < B.h.nops; o++) {
           const Op op = patched(A.ops[B.op_first + o], pt);
-          apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, 0);
+          apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, 0, (const double2*)B.h.dtab);
           __syncthreads();
         }
       }
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
           __syncthreads();
           for (int o = 0; o < B.h.nops; o++) {
             const Op op = patched(A.ops[B.op_first + o], pt);
-            apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, base);
+            apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, base, (const double2*)B.h.dtab);
             __syncthreads();
           }
           for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
@@ -380,6 +380,11 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B) {
     for (int p = 0; p < S.npasses; p++) {
       BPass bp;
       bp.h = S.passes[p].h;
+      if (bp.h.flags & PF_DYADIC) {
+        cudaError_t e;
+        bp.h.dtab = dyadic_tables(&e);
+        if (!bp.h.dtab) return fail(LQ_ERR_CUDA, "dyadic tables: %s", cudaGetErrorString(e));
+      }
       bp.op_first = (int)B.ops.size();
       bp.coef_first = (int)B.coef.size();
       for (int o = 0; o < bp.h.nops; o++) B.ops.push_back(S.passes[p].ops[o]);
@@ -388,6 +393,7 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B) {
         const Op& d = S.passes[p].ops[o];
         if (d.type == OP_PAIR_GEN) ncoef = std::max(ncoef, (int)d.cidx + 8);
         if (d.type == OP_QUAD_GEN) ncoef = std::max(ncoef, (int)d.cidx + 32);
+        if (d.type == OP_DPHASE) ncoef = std::max(ncoef, (int)d.cidx + 4 * (int)d.x_loc);
       }
       for (int c = 0; c < ncoef; c++) B.coef.push_back(S.passes[p].coef[c]);
       B.passes.push_back(bp);

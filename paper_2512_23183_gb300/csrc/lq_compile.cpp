@@ -152,6 +152,19 @@ static LOp diag_op(uint8_t type, uint64_t cm, uint64_t cv, double a, double b) {
   return o;
 }
 
+// Weight w with angle = 2 pi w / 2^34 (mod 2^34) if the angle is an exact
+// dyadic multiple of 2 pi / 2^34, else -1.
+static int64_t dyadic_weight(double angle) {
+  const double PI = 3.14159265358979323846;
+  double w = angle / PI * std::ldexp(1.0, DYADIC_BITS - 1);
+  if (!(std::fabs(w) < std::ldexp(1.0, 60)) || w != std::floor(w)) return -1;
+  int64_t iw = (int64_t)w;
+  const int64_t M = (int64_t)1 << DYADIC_BITS;
+  iw %= M;
+  if (iw < 0) iw += M;
+  return iw;
+}
+
 lq_status lower_gate(const lq_gate& g, int n, double theta, Lowered& L) {
   L = Lowered();
   int b[3] = {0, 0, 0};
@@ -172,22 +185,28 @@ lq_status lower_gate(const lq_gate& g, int n, double theta, Lowered& L) {
       break;
     case LQ_X: o = pauli_op(m0, 0, 0, PM_PERM); break;
     case LQ_Y: o = pauli_op(m0, m0, 1, PM_PERM); break;
-    case LQ_Z: o = diag_op(OP_SIGN, m0, m0, 0, 0); break;
-    case LQ_S: o = diag_op(OP_MULI, m0, m0, 0, 0); o.mode = 1; break;
-    case LQ_SDG: o = diag_op(OP_MULI, m0, m0, 0, 0); o.mode = 3; break;
-    case LQ_T: o = diag_op(OP_PHASE, m0, m0, R2, R2); break;
-    case LQ_TDG: o = diag_op(OP_PHASE, m0, m0, R2, -R2); break;
+    case LQ_Z: o = diag_op(OP_SIGN, m0, m0, 0, 0); o.dy = (int64_t)1 << 33; break;
+    case LQ_S: o = diag_op(OP_MULI, m0, m0, 0, 0); o.mode = 1; o.dy = (int64_t)1 << 32; break;
+    case LQ_SDG: o = diag_op(OP_MULI, m0, m0, 0, 0); o.mode = 3; o.dy = (int64_t)3 << 32; break;
+    case LQ_T: o = diag_op(OP_PHASE, m0, m0, R2, R2); o.dy = (int64_t)1 << 31; break;
+    case LQ_TDG: o = diag_op(OP_PHASE, m0, m0, R2, -R2); o.dy = (int64_t)7 << 31; break;
     case LQ_RX: o = pauli_op(m0, 0, 0, ac.mode0); o.a = ac.a0; o.b = ac.b0; break;
     case LQ_RY: o = pauli_op(m0, m0, 1, ac.mode0); o.a = ac.a0; o.b = ac.b0; break;
-    case LQ_RZ: case LQ_P: o = diag_op(OP_PHASE, m0, m0, ac.a0, ac.b0); break;
+    case LQ_RZ: case LQ_P:
+      o = diag_op(OP_PHASE, m0, m0, ac.a0, ac.b0);
+      o.dy = dyadic_weight(theta);
+      break;
     case LQ_U1:
       o.type = OP_PAIR_GEN; o.g0 = b[0]; o.ncoef = 8;
       for (int i = 0; i < 8; i++) o.coef[i] = g.mat[i];
       break;
     case LQ_CNOT: o = pauli_op(m1, 0, 0, PM_PERM); o.cm = m0; o.cv = m0; break;
     case LQ_CY: o = pauli_op(m1, m1, 1, PM_PERM); o.cm = m0; o.cv = m0; break;
-    case LQ_CZ: o = diag_op(OP_SIGN, m0 | m1, m0 | m1, 0, 0); break;
-    case LQ_CP: o = diag_op(OP_PHASE, m0 | m1, m0 | m1, ac.a0, ac.b0); break;
+    case LQ_CZ: o = diag_op(OP_SIGN, m0 | m1, m0 | m1, 0, 0); o.dy = (int64_t)1 << 33; break;
+    case LQ_CP:
+      o = diag_op(OP_PHASE, m0 | m1, m0 | m1, ac.a0, ac.b0);
+      o.dy = dyadic_weight(theta);
+      break;
     case LQ_SWAP: o.type = OP_SWAP; o.g0 = b[0]; o.g1 = b[1]; break;
     case LQ_CRX:
       o = pauli_op(m1, 0, 0, PM_GEN); o.a = ac.a0; o.b = ac.b0; o.cm = m0; o.cv = m0;
@@ -219,6 +238,58 @@ lq_status lower_gate(const lq_gate& g, int n, double theta, Lowered& L) {
   return LQ_OK;
 }
 
+// Merge runs of consecutive fixed dyadic diagonal ops (phases that are exact
+// multiples of 2 pi / 2^34: CP(pi/2^k), T, S, Z, CZ, ...) into one OP_DPHASE
+// when that needs fewer FP64 operations: the merged op costs at most two
+// complex multiplies on the amplitudes meeting the factors' common
+// condition, a separate phase op one complex multiply on its own fraction.
+static bool dyadic_diag(const LOp& o) {
+  return o.fixed && o.dy >= 0 && (o.type == OP_PHASE || o.type == OP_SIGN || o.type == OP_MULI);
+}
+
+void merge_dyadic(std::vector<LOp>& ops, int n) {
+  std::vector<LOp> out;
+  out.reserve(ops.size());
+  std::size_t i = 0;
+  while (i < ops.size()) {
+    if (!dyadic_diag(ops[i])) {
+      out.push_back(ops[i++]);
+      continue;
+    }
+    std::size_t j = i;
+    while (j < ops.size() && dyadic_diag(ops[j])) j++;
+    // common condition: bits every factor requires with the same value
+    uint64_t cm = ~0ull, cv = 0, all = 0;
+    double separate = 0;
+    for (std::size_t k = i; k < j; k++) {
+      cm &= ops[k].cm;
+      all |= ops[k].cm;
+      separate += op_flops(ops[k], n);
+    }
+    for (std::size_t k = i; k < j; k++) cm &= ~(ops[k].cv ^ ops[i].cv);
+    cv = ops[i].cv & cm;
+    LOp m;
+    m.type = OP_DPHASE;
+    m.cm = cm;
+    m.cv = cv;
+    m.z = all & ~cm;
+    m.fixed = true;
+    for (std::size_t k = i; k < j; k++) {
+      m.dfac.push_back(ops[k].cm);
+      m.dfac.push_back(ops[k].cv);
+      m.dfac.push_back((uint64_t)ops[k].dy);
+    }
+    m.ncoef = 4 * (int)(j - i);
+    if (j - i >= 2 && m.ncoef <= MAX_COEF / 2 && op_flops(m, n) < separate) {
+      out.push_back(m);
+    } else {
+      for (std::size_t k = i; k < j; k++) out.push_back(ops[k]);
+    }
+    i = j;
+  }
+  ops.swap(out);
+}
+
 // Magnitude window of the deferred scalar; outside it the magnitude is applied
 // by an explicit OP_SCALE so stored amplitudes stay far from overflow.
 static const double kScaleLo = 1e-100, kScaleHi = 1e100;
@@ -237,6 +308,7 @@ lq_status lower_circuit(int n, const lq_gate* gates, int ng, const double* param
     if (st) return st;
     for (int j = 0; j < L.nops; j++) {
       L.op[j].gate = g;
+      L.op[j].fixed = gates[g].param < 0;
       ops.push_back(L.op[j]);
     }
     double nr = zr * L.zr - zi * L.zi, ni = zr * L.zi + zi * L.zr;
@@ -253,6 +325,7 @@ lq_status lower_circuit(int n, const lq_gate* gates, int ng, const double* param
       zi /= mag;
     }
   }
+  merge_dyadic(ops, n);
   LOp* out = new LOp[ops.size() > 0 ? ops.size() : 1];
   for (std::size_t i = 0; i < ops.size(); i++) out[i] = ops[i];
   *ops_out = out;
@@ -281,6 +354,7 @@ double op_flops(const LOp& o, int n) {
     case OP_PARITY: return 6.0 * N * 0.5 * frac;
     case OP_SCALE: return ((o.mode & 1) ? 2.0 : 6.0) * N;
     case OP_GRAD: return 4.0 * N;
+    case OP_DPHASE: return 12.0 * N * frac;                // table combine + multiply
     default: return 0.0;                                   // sign flips, i^k, swaps
   }
 }
@@ -302,6 +376,31 @@ static uint32_t to_local(uint64_t mask, const int* pos) {
   return r;
 }
 
+static uint64_t dbits(double v) {
+  uint64_t u;
+  std::memcpy(&u, &v, sizeof u);
+  return u;
+}
+static double bitsd(uint64_t u) {
+  double v;
+  std::memcpy(&v, &u, sizeof v);
+  return v;
+}
+
+// Factor list of an OP_DPHASE in the pass coefficient pool: per factor
+// (tile-local cm | cv << 32, CTA-bit cm, CTA-bit cv, weight), as raw bits.
+static void fill_dphase(double* pool, const LOp& s, uint64_t tile, const int* pos) {
+  const std::size_t nf = s.dfac.size() / 3;
+  for (std::size_t f = 0; f < nf; f++) {
+    uint64_t cm = s.dfac[3 * f], cv = s.dfac[3 * f + 1], w = s.dfac[3 * f + 2];
+    uint64_t loc = (uint64_t)to_local(cm & tile, pos) | ((uint64_t)to_local(cv & tile, pos) << 32);
+    pool[4 * f + 0] = bitsd(loc);
+    pool[4 * f + 1] = bitsd(cm & ~tile);
+    pool[4 * f + 2] = bitsd(cv & ~tile);
+    pool[4 * f + 3] = bitsd(w);
+  }
+}
+
 static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef_at) {
   std::memset(&d, 0, sizeof d);
   d.type = s.type;
@@ -310,7 +409,7 @@ static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef
   d.b1 = s.g1 >= 0 ? (uint8_t)pos[s.g1] : (uint8_t)s.sub;
   if (s.type == OP_GRAD)
     d.cidx = (uint32_t)s.slot;
-  else if (s.type == OP_PAIR_GEN || s.type == OP_QUAD_GEN)
+  else if (s.type == OP_PAIR_GEN || s.type == OP_QUAD_GEN || s.type == OP_DPHASE)
     d.cidx = (uint32_t)coef_at;
   else
     d.cidx = (uint32_t)s.gate;
@@ -318,7 +417,7 @@ static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef
   d.cv_loc = to_local(s.cv & tile, pos);
   d.cm_glob = s.cm & ~tile;
   d.cv_glob = s.cv & ~tile;
-  d.x_loc = to_local(s.x, pos);
+  d.x_loc = s.type == OP_DPHASE ? (uint32_t)(s.dfac.size() / 3) : to_local(s.x, pos);
   d.z_loc = to_local(s.z & tile, pos);
   d.z_glob = s.z & ~tile;
   d.a = s.a;
@@ -407,7 +506,12 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
     int coef_at = 0, cnt = 0;
     for (int idx : B.idx) {
       fill_op(P.ops[cnt], ops[idx], B.tile, pos, coef_at);
-      for (int c = 0; c < ops[idx].ncoef; c++) P.coef[coef_at + c] = ops[idx].coef[c];
+      if (ops[idx].type == OP_DPHASE) {
+        fill_dphase(P.coef + coef_at, ops[idx], B.tile, pos);
+        P.h.flags |= PF_DYADIC;
+      }
+      else
+        for (int c = 0; c < ops[idx].ncoef; c++) P.coef[coef_at + c] = ops[idx].coef[c];
       coef_at += ops[idx].ncoef;
       out.op_src[p * MAX_OPS + cnt] = idx;
       cnt++;

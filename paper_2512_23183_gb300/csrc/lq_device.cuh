@@ -59,11 +59,14 @@ __device__ __forceinline__ uint64_t deposit(uint64_t v, const int8_t* pos, int c
   return r;
 }
 
+// All threads of the block call it; the caller synchronises.
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
-// are `base`.  All threads of the block call it; the caller synchronises.
+// are `base`; dtab: dyadic phase tables (hi: 2^17 entries exp(2 pi i h / 2^17),
+// lo: 2^17 entries exp(2 pi i l / 2^34)).
 template <int BLOCK>
 __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, const Op& op,
-                                         const double* __restrict__ coef, uint64_t base) {
+                                         const double* __restrict__ coef, uint64_t base,
+                                         const double2* __restrict__ dtab) {
   const uint32_t tid = threadIdx.x;
   if ((base & op.cm_glob) != op.cv_glob) return;  // CTA-level condition
   const int zs = __popcll(base & op.z_glob) & 1;
@@ -222,6 +225,44 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
           s |= (uint32_t)(((__popc(s & z) + zs) & 1) ^ 1) << hz;
           sm[s] = cmul(sm[s], wr, wi);
         }
+      }
+      break;
+    }
+    case OP_DPHASE: {
+      // E(s) = sum of the weights of the factors whose conditions hold, mod
+      // 2^34; the phase exp(2 pi i E / 2^34) = hi[E >> 17] * lo[E & (2^17-1)]
+      const int nf = (int)op.x_loc;
+      const double* F = coef + op.cidx;
+      const uint32_t cnt = T >> __popc(cm);
+      const uint64_t MASK = (1ull << DYADIC_BITS) - 1ull, LOMASK = (1ull << DYADIC_HALF) - 1ull;
+      uint64_t e0 = 0;   // factors decided by CTA bits alone
+      for (int f = 0; f < nf; f++) {
+        const uint64_t loc = (uint64_t)__double_as_longlong(F[4 * f]);
+        const uint64_t gm = (uint64_t)__double_as_longlong(F[4 * f + 1]);
+        const uint64_t gv = (uint64_t)__double_as_longlong(F[4 * f + 2]);
+        if ((uint32_t)loc == 0 && (base & gm) == gv) e0 += (uint64_t)__double_as_longlong(F[4 * f + 3]);
+      }
+      for (uint32_t j = tid; j < cnt; j += BLOCK) {
+        const uint32_t s = expand(j, cm, cv);
+        uint64_t e = e0;
+        for (int f = 0; f < nf; f++) {
+          const uint64_t loc = (uint64_t)__double_as_longlong(F[4 * f]);
+          const uint32_t lm = (uint32_t)loc, lv = (uint32_t)(loc >> 32);
+          if (lm == 0) continue;
+          const uint64_t gm = (uint64_t)__double_as_longlong(F[4 * f + 1]);
+          const uint64_t gv = (uint64_t)__double_as_longlong(F[4 * f + 2]);
+          if ((s & lm) == lv && (base & gm) == gv)
+            e += (uint64_t)__double_as_longlong(F[4 * f + 3]);
+        }
+        e &= MASK;
+        if (e == 0) continue;
+        double2 w = dtab[e >> DYADIC_HALF];
+        const uint64_t lo = e & LOMASK;
+        if (lo) {
+          const double2 wl = dtab[(1u << DYADIC_HALF) + lo];
+          w = cmul(w, wl.x, wl.y);
+        }
+        sm[s] = cmul(sm[s], w.x, w.y);
       }
       break;
     }

@@ -27,6 +27,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/lq.h"
 
@@ -52,6 +53,9 @@ enum OpType : uint8_t {
   OP_PARITY,      // multiply amplitudes with odd popcount(idx & z) by (a + i b)
   OP_SCALE,       // multiply every amplitude by (a + i b) (mode 1: b == 0)
   OP_GRAD,        // adjoint: accumulate Im <lam| G |psi> into slot cidx
+  OP_DPHASE,      // merged dyadic phases: exp(2 pi i E(idx) / 2^34), E = sum of
+                  // integer weights of the factors whose conditions hold
+                  // (x_loc factors at coef[cidx..], 4 doubles each)
   OP_TYPE_COUNT
 };
 
@@ -83,6 +87,8 @@ struct Op {
 };
 static_assert(sizeof(Op) == 64, "Op must stay 64 bytes");
 
+constexpr int DYADIC_BITS = 34;    // dyadic phases are multiples of 2 pi / 2^34
+constexpr int DYADIC_HALF = 17;    // two-level table: 2^17 + 2^17 entries
 constexpr int MAX_TILE_BITS = 13;   // 2^13 amplitudes = 128 KiB of shared memory
 constexpr int MAX_OPS = 384;        // per pass (kernel-parameter budget)
 constexpr int MAX_COEF = 512;       // doubles per pass coefficient pool
@@ -94,12 +100,14 @@ struct PassHeader {
   int32_t nobits;
   int32_t flags;          // PF_* below
   uint64_t ntiles;        // 2^(n-k)
+  const void* dtab;       // dyadic phase tables (device), set at launch
   int8_t tbits[16];       // tile-local bit j -> global bit position
   int8_t obits[48];       // CTA bits (global positions), ascending
 };
 enum PassFlags : int32_t {
   PF_INIT_ZERO = 1,       // do not load: start from |0...0> (whole-state tile)
   PF_NO_STORE = 2,        // do not store the tile back
+  PF_DYADIC = 4,          // the pass has OP_DPHASE ops (needs dtab)
 };
 
 struct PassParams {
@@ -124,6 +132,11 @@ struct LOp {
   int slot = -1;                 // gradient slot (OP_GRAD)
   double fr = 1, fi = 0;         // deferred factor this op contributes to the
                                  // global scalar (first op of a gate)
+  int64_t dy = -1;               // dyadic phase weight (angle = 2 pi dy / 2^34) of a
+                                 // fixed diagonal op, -1 if not dyadic
+  bool fixed = false;            // from a gate without a parameter
+  // OP_DPHASE factors: (cm, cv, weight) triples, global bits
+  std::vector<uint64_t> dfac;
   uint64_t mix() const;          // bits that must lie inside the tile
   uint64_t diag() const;         // bits only read (conditions, phases)
 };
@@ -173,6 +186,9 @@ struct Schedule {
 // circuit with a unit scalar).
 lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, double zi,
                        const ScheduleOptions& opt, Schedule& out);
+
+// Merge runs of fixed dyadic diagonal ops into OP_DPHASE where cheaper.
+void merge_dyadic(std::vector<LOp>& ops, int n);
 
 // Validate and lower a whole circuit at the given parameters.  The caller
 // owns *ops_out (delete[]).  (*zr, *zi) is the product of deferred factors.

@@ -3,7 +3,9 @@
 // Alg. 4), and the Pauli-sum kernels (<H>, H psi; Sec. VI-A, Sec. VII-A-2).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "lq_device.cuh"
 #include "lq_kernels.h"
@@ -25,6 +27,46 @@ cudaError_t launch_init_basis(double2* amps, int n, uint64_t basis, cudaStream_t
   int grid = (int)(blocks < (uint64_t)sm_count() * 16 ? blocks : (uint64_t)sm_count() * 16);
   init_basis_kernel<<<grid, 256, 0, s>>>(amps, N, basis);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------- dyadic phase tables
+
+// g_dyadic[h] = exp(2 pi i h / 2^17), g_dyadic[2^17 + l] = exp(2 pi i l / 2^34),
+// so exp(2 pi i E / 2^34) = g_dyadic[E >> 17] * g_dyadic[2^17 + (E & (2^17-1))].
+__device__ double2 g_dyadic[2 << DYADIC_HALF];
+
+__global__ void dyadic_table_kernel() {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (2u << DYADIC_HALF)) return;
+  const uint32_t j = i & ((1u << DYADIC_HALF) - 1u);
+  // angle / pi = 2 j / 2^17 (high table) or 2 j / 2^34 (low table), exact
+  const double x = (i >> DYADIC_HALF) ? std::ldexp((double)j, 1 - DYADIC_BITS)
+                                      : std::ldexp((double)j, 1 - DYADIC_HALF);
+  double sn, cs;
+  sincospi(x, &sn, &cs);
+  g_dyadic[i] = make_double2(cs, sn);
+}
+
+// Device address of the tables of the current device, filling them on first
+// use (synchronously, so no stream can read them before they are complete).
+const double2* dyadic_tables(cudaError_t* err) {
+  static std::mutex mu;
+  static const double2* ptr[64] = {nullptr};
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_dyadic);
+    if (*err != cudaSuccess) return nullptr;
+    dyadic_table_kernel<<<(2u << DYADIC_HALF) / 256, 256>>>();
+    *err = cudaGetLastError();
+    if (*err == cudaSuccess) *err = cudaDeviceSynchronize();
+    if (*err != cudaSuccess) return nullptr;
+    ptr[dev] = (const double2*)p;
+  }
+  return ptr[dev];
 }
 
 // ----------------------------------------------------------- tile passes
@@ -63,7 +105,7 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
     __syncthreads();
     if (patches == nullptr) {
       for (int o = 0; o < nops; o++) {
-        apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base);
+        apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab);
         __syncthreads();
       }
     } else {
@@ -88,7 +130,7 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
           op.b = ar * pt.zi + ai * pt.zr;
           op.mode &= ~1;
         }
-        apply_op<BLOCK>(sm, T, op, P.coef, base);
+        apply_op<BLOCK>(sm, T, op, P.coef, base, (const double2*)P.h.dtab);
         __syncthreads();
       }
     }
@@ -118,7 +160,17 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
   int per_sm = smem <= 16384 ? 8 : smem <= 32768 ? 6 : smem <= 65536 ? 3 : 1;
   uint64_t cap = (uint64_t)sm_count() * per_sm;
   int grid = (int)(total < cap ? total : cap);
-  pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, patches);
+  if (P.h.flags & PF_DYADIC) {
+    cudaError_t e;
+    const double2* t = dyadic_tables(&e);
+    if (!t) return e;
+    static thread_local PassParams Q;   // launch copy carrying the table address
+    Q = P;
+    Q.h.dtab = t;
+    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(Q, state, stride, nstates, patches);
+  } else {
+    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, patches);
+  }
   return cudaGetLastError();
 }
 
@@ -180,8 +232,8 @@ __global__ void __launch_bounds__(BLOCK) pass2_kernel(const __grid_constant__ Pa
           partial[(uint64_t)op.cidx * gridDim.x + blockIdx.x] += sum;
         }
       } else {
-        apply_op<BLOCK>(A, T, op, P.coef, base);
-        apply_op<BLOCK>(B, T, op, P.coef, base);
+        apply_op<BLOCK>(A, T, op, P.coef, base, (const double2*)P.h.dtab);
+        apply_op<BLOCK>(B, T, op, P.coef, base, (const double2*)P.h.dtab);
       }
       __syncthreads();
     }
@@ -216,7 +268,17 @@ cudaError_t launch_pass2(const PassParams& P, double2* psi, double2* lam, double
   }
   if (P.h.k > 12) return cudaErrorInvalidValue;
   size_t smem = 2 * (sizeof(double2) << P.h.k);
-  pass2_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, psi, lam, partial);
+  if (P.h.flags & PF_DYADIC) {
+    cudaError_t e;
+    const double2* t = dyadic_tables(&e);
+    if (!t) return e;
+    static thread_local PassParams Q;
+    Q = P;
+    Q.h.dtab = t;
+    pass2_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(Q, psi, lam, partial);
+  } else {
+    pass2_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, psi, lam, partial);
+  }
   return cudaGetLastError();
 }
 

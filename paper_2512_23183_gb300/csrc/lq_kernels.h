@@ -75,6 +75,7 @@ lq_status batch_run(const std::vector<HostProblem>& hps, void* ws, std::size_t w
 // --------------------------------------------------------------- launchers
 
 int sm_count();
+const double2* dyadic_tables(cudaError_t* err);
 int expval_grid(int n);
 
 cudaError_t launch_init_basis(double2* amps, int n, uint64_t basis, cudaStream_t s);

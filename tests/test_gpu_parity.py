@@ -252,3 +252,30 @@ def test_trotter(lq, n, steps):
     t = lq.new_state(n, x0)
     lq.trotter_evolve(t, n, static, field, A, omega, dt, steps)
     np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
+
+
+@pytest.mark.parametrize("n,seed", [(3, 1), (9, 2), (14, 3), (16, 4)])
+def test_fixed_dyadic_phase_runs(lq, n, seed):
+    # runs of fixed dyadic diagonal gates (merged into one table-driven phase
+    # op when cheaper) between H layers, with controls on tile and CTA bits
+    rng = np.random.default_rng(seed)
+    gates = []
+    for layer in range(4):
+        for q in range(n):
+            gates.append(W.G("H", q))
+        for _ in range(3 * n):
+            kind = ["CP", "CP", "P", "T", "TDG", "S", "Z", "CZ", "RZ"][rng.integers(9)]
+            k = int(rng.integers(1, 12))
+            ang = float(rng.choice([1, -1]) * np.pi / 2 ** k)
+            if kind in ("CP", "CZ"):
+                a, b = rng.choice(n, 2, replace=False) if n > 1 else (0, 0)
+                gates.append(W.G(kind, a, b, angle=ang if kind == "CP" else 0.0))
+            else:
+                gates.append(W.G(kind, int(rng.integers(n)),
+                                 angle=ang if kind in ("P", "RZ") else 0.0))
+    gates = [g for g in gates if len(set(g.qubits)) == len(g.qubits)]
+    psi = W.gaussian_state(n, 60 + seed)
+    want = oracle.apply_circuit(psi.copy(), n, gates)
+    t = dev(psi)
+    lq.apply_circuit(t, n, gates)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
