@@ -255,6 +255,21 @@ class Step:
         return e8, g8
 
 
+def aggregate(ms_local, bytes_local, world, device):
+    """Step time = max over ranks (all ranks run the same step on their own
+    GPU: replicas, no data-path collective); value = all ranks' bytes / that
+    time, in GB/s."""
+    import torch
+
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, world * bytes_local / (ms * 1e-3) / 1e9
+
+
 def bench_lq(a, rank, world, device):
     import torch
 
@@ -289,12 +304,7 @@ def bench_lq(a, rank, world, device):
         for i, nm in enumerate(names):
             if i + 1 < 8:
                 seg_ms[nm] += e[i].elapsed_time(e[i + 1])
-    ms = total_ms / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * step.bytes / (ms * 1e-3) / 1e9
+    ms, value = aggregate(total_ms / a.steps, step.bytes, world, device)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     rows = {}

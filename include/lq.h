@@ -285,6 +285,28 @@ lq_status lq_batch_param_shift(const lq_problem* problems, int count, void* work
                                size_t ws_bytes, lq_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * VQE outer loop (Sec. VI-B): Adam on E(theta), each gradient on the GPU.
+ * The paper's settings are lr = 1e-2, at most 350 iterations, tolerance 1e-7
+ * on the energy change; beta1 = 0.9, beta2 = 0.999, eps = 1e-8 are Adam's
+ * usual constants.  method 0: adjoint gradient; 1: batched parameter shift.
+ */
+typedef struct {
+  double lr, beta1, beta2, eps, tol;
+  int32_t max_iters, method;
+} lq_adam_options;
+
+size_t lq_vqe_workspace_size(int n, int ng, int np, int nt, int method);
+
+/* params: host, in/out (updated in place).  energies: host, max_iters
+ * doubles; energies[i] is E at the parameters of iteration i+1 (before its
+ * update).  *iters = gradient evaluations made (the loop stops at max_iters
+ * or when |E_t - E_{t-1}| < tol, without updating after that evaluation). */
+lq_status lq_vqe_adam(int n, const lq_gate* gates, int ng, double* params, int np,
+                      const lq_pauli_term* terms, int nt, const lq_adam_options* opt,
+                      double* energies, int* iters, void* workspace, size_t ws_bytes,
+                      lq_stream stream);
+
+/* ---------------------------------------------------------------------------
  * Serving: a continuous-batching request server (spec addition; the
  * paper has no serving layer).  Requests carry one circuit, its parameters
  * and a Pauli sum, energy only or energy and gradient (adjoint).  The server

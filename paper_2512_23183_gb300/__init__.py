@@ -46,6 +46,11 @@ class LqProblem(ctypes.Structure):
                 ("grad", ctypes.POINTER(c_double))]
 
 
+class LqAdamOptions(ctypes.Structure):
+    _fields_ = [("lr", c_double), ("beta1", c_double), ("beta2", c_double), ("eps", c_double),
+                ("tol", c_double), ("max_iters", c_int32), ("method", c_int32)]
+
+
 class LqRequest(ctypes.Structure):
     _fields_ = [("n", c_int32), ("ng", c_int32), ("np", c_int32), ("nt", c_int32),
                 ("want_grad", c_int32), ("reserved", c_int32),
@@ -85,7 +90,8 @@ EXPORTS = [
     "lq_adjoint_workspace_size", "lq_adjoint_grad", "lq_trotter_evolve",
     "lq_batch_workspace_size", "lq_batch_param_shift", "lq_circuit_plan", "lq_qft_plan",
     "lq_expval_pauli_sum_noalloc", "lq_server_footprint", "lq_server_create",
-    "lq_server_submit", "lq_server_wait", "lq_server_destroy",
+    "lq_server_submit", "lq_server_wait", "lq_server_destroy", "lq_vqe_workspace_size",
+    "lq_vqe_adam",
 ]
 
 
@@ -139,6 +145,11 @@ def load(build_if_missing=True):
     L.lq_batch_workspace_size.argtypes = [P(LqProblem), ctypes.c_int]
     L.lq_batch_workspace_size.restype = c_size_t
     L.lq_batch_param_shift.argtypes = [P(LqProblem), ctypes.c_int, c_void_p, c_size_t, c_void_p]
+    L.lq_vqe_workspace_size.argtypes = [ctypes.c_int] * 5
+    L.lq_vqe_workspace_size.restype = c_size_t
+    L.lq_vqe_adam.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
+                              P(LqPauliTerm), ctypes.c_int, P(LqAdamOptions), P(c_double),
+                              P(ctypes.c_int), c_void_p, c_size_t, c_void_p]
     L.lq_server_footprint.argtypes = [ctypes.c_int] * 5
     L.lq_server_footprint.restype = c_size_t
     L.lq_server_create.argtypes = [c_void_p, c_size_t, ctypes.c_int, P(c_void_p)]
@@ -389,6 +400,25 @@ def batch_param_shift(problems, device="cuda", stream=None, workspace=None):
         pb.energy = float(e[0])
         pb.grad = gr[: pb.params.size].copy()
     return problems
+
+
+def vqe_adam(n, gates, params, terms, lr=1e-2, max_iters=350, tol=1e-7, method=0,
+             beta1=0.9, beta2=0.999, eps=1e-8, device="cuda", stream=None):
+    """Minimise E(theta) with Adam (Sec. VI-B settings by default).  Returns
+    (final params, energies per iteration)."""
+    L = load()
+    g = pack_gates(gates)
+    t = pack_terms(terms, n)
+    p = np.array(params, np.float64, copy=True)
+    need = L.lq_vqe_workspace_size(n, len(gates), p.size, len(terms), int(method))
+    ws = _workspace(need, device)
+    opt = LqAdamOptions(lr, beta1, beta2, eps, tol, int(max_iters), int(method))
+    es = np.zeros(max_iters)
+    it = ctypes.c_int(0)
+    _check(L.lq_vqe_adam(n, g, len(gates), p.ctypes.data_as(ctypes.POINTER(c_double)), p.size, t,
+                         len(terms), ctypes.byref(opt), es.ctypes.data_as(ctypes.POINTER(c_double)),
+                         ctypes.byref(it), _ptr(ws), ws.numel(), _stream(stream)))
+    return p, es[: it.value].copy()
 
 
 class Server:

@@ -211,13 +211,10 @@ lq_status lq_adjoint_grad(int n, const lq_gate* gates, int ng, const double* par
   {
     double ar = 1, ai = 0;
     for (int ps = 0; ps < S.npasses; ps++)
-      for (int o = 0; o < S.passes[ps].h.nops; o++) {
-        int src = S.op_src[ps * MAX_OPS + o];
-        if (src < 0) continue;
-        const LOp& l = ops[src];
+      for (const LOp& l : S.pass_ops[ps]) {
         if (l.type == OP_GRAD) {
           factor[l.slot] = l.a * (ar * ar + ai * ai);
-        } else {
+        } else if (!(l.type == OP_SCALE && (l.mode & 2))) {
           double nr2 = ar * l.fr - ai * l.fi, ni2 = ar * l.fi + ai * l.fr;
           ar = nr2;
           ai = ni2;

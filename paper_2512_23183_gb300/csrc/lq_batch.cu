@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "lq_coefs.h"
@@ -365,6 +366,7 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B) {
     ScheduleOptions opt;
     opt.k = n <= BATCH_SMEM_BITS ? n : BATCH_TILE_BITS;
     opt.force_scale = true;
+    opt.merge_params = false;   // shifted circuits patch individual gates
     Schedule S;
     st = schedule_ops(n, ops, nops, zr, zi, opt, S);
     double flops = 0;
@@ -394,6 +396,7 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B) {
         if (d.type == OP_PAIR_GEN) ncoef = std::max(ncoef, (int)d.cidx + 8);
         if (d.type == OP_QUAD_GEN) ncoef = std::max(ncoef, (int)d.cidx + 32);
         if (d.type == OP_DPHASE) ncoef = std::max(ncoef, (int)d.cidx + 4 * (int)d.x_loc);
+        if (d.type == OP_LPHASE) ncoef = std::max(ncoef, (int)d.cidx + 5 * (int)d.x_loc);
       }
       for (int c = 0; c < ncoef; c++) B.coef.push_back(S.passes[p].coef[c]);
       B.passes.push_back(bp);
@@ -481,6 +484,41 @@ static std::size_t batch_bytes(const BatchPlan& B, int grid) {
   return b;
 }
 
+// ------------------------------------------------------ graph replay
+//
+// A batch run is four stream operations: upload the program image, reset the
+// two counters, the persistent kernel, download the results.  They are
+// captured once per layout (workspace address, section sizes, grid) into a
+// CUDA graph on an internal stream of the device and replayed; a replay
+// only rewrites the pinned staging image (new angles give new coefficients,
+// never a new layout).  Events order the replay after the caller's stream
+// work and the caller's stream after the replay.
+
+struct GraphEntry {
+  int device = -1;
+  void* ws = nullptr;
+  std::vector<std::size_t> key;
+  cudaGraphExec_t exec = nullptr;
+  char* h_image = nullptr;      // pinned
+  double* h_out = nullptr;      // pinned
+  std::size_t image = 0, nout = 0;
+  uint64_t last_use = 0;
+};
+
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;
+static uint64_t g_graph_clock = 0;
+static cudaStream_t g_graph_stream[64] = {nullptr};
+static cudaEvent_t g_ev_in[64] = {nullptr}, g_ev_out[64] = {nullptr};
+constexpr std::size_t kMaxGraphs = 8;
+
+static void drop_entry(GraphEntry& e) {
+  if (e.exec) cudaGraphExecDestroy(e.exec);
+  if (e.h_image) cudaFreeHost(e.h_image);
+  if (e.h_out) cudaFreeHost(e.h_out);
+  e = GraphEntry();
+}
+
 // Run the batch; results (per problem E then grad) into host vector `out`.
 static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_bytes,
                            cudaStream_t s, std::vector<double>& out) {
@@ -490,12 +528,14 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
   char* p = (char*)workspace;
   BatchArgs A;
   std::memset(&A, 0, sizeof A);
-  std::vector<char> host;   // program image uploaded with one copy
+  std::vector<std::size_t> key;
   std::size_t off = 0;
+  struct Sec { const void* src; std::size_t n, cap; };
+  std::vector<Sec> secs;
   auto place = [&](const void* src, std::size_t n, std::size_t cap) {
     std::size_t at = off;
-    host.resize(off + cap);
-    if (n) std::memcpy(host.data() + at, src, n);
+    secs.push_back({src, n, cap});
+    key.push_back(cap);
     off += cap;
     return p + at;
   };
@@ -526,19 +566,83 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
   A.scratch_stride = B.nmax_scratch > 0 ? (1ull << B.nmax_scratch) : 0;
   A.nitems = (int)B.items.size();
   A.nprobs = (int)B.probs.size();
-  LQ_CUDA(cudaMemcpyAsync(p, host.data(), image, cudaMemcpyHostToDevice, s));
-  LQ_CUDA(cudaMemsetAsync(A.counters, 0, sizeof(int32_t) * 2, s));
+  const std::size_t smem = sizeof(double2) << B.kmax;
+  key.push_back(B.patches.size());
+  key.push_back((std::size_t)B.nout);
+  key.push_back((std::size_t)grid);
+  key.push_back(smem);
+  key.push_back((std::size_t)A.scratch_stride);
+  key.push_back((std::size_t)A.nitems);
+  key.push_back((std::size_t)A.nprobs);
+  int dev = 0;
+  LQ_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(LQ_ERR_INVALID_ARG, "device %d", dev);
   static bool configured = false;
   if (!configured) {
     LQ_CUDA(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(double2) << BATCH_SMEM_BITS)));
     configured = true;
   }
-  batch_kernel<256><<<grid, 256, sizeof(double2) << B.kmax, s>>>(A);
-  LQ_CUDA(cudaGetLastError());
-  out.assign((std::size_t)B.nout, 0.0);
-  LQ_CUDA(cudaMemcpyAsync(out.data(), A.out, sizeof(double) * B.nout, cudaMemcpyDeviceToHost, s));
-  LQ_CUDA(cudaStreamSynchronize(s));
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  if (!g_graph_stream[dev]) {
+    LQ_CUDA(cudaStreamCreateWithFlags(&g_graph_stream[dev], cudaStreamNonBlocking));
+    LQ_CUDA(cudaEventCreateWithFlags(&g_ev_in[dev], cudaEventDisableTiming));
+    LQ_CUDA(cudaEventCreateWithFlags(&g_ev_out[dev], cudaEventDisableTiming));
+  }
+  cudaStream_t gs = g_graph_stream[dev];
+  GraphEntry* E = nullptr;
+  for (auto& e : g_graphs)
+    if (e.device == dev && e.ws == workspace && e.key == key) E = &e;
+  if (!E) {
+    // capture a new graph for this layout (evict the least recently used)
+    if (g_graphs.size() >= kMaxGraphs) {
+      std::size_t lru = 0;
+      for (std::size_t i = 1; i < g_graphs.size(); i++)
+        if (g_graphs[i].last_use < g_graphs[lru].last_use) lru = i;
+      drop_entry(g_graphs[lru]);
+      g_graphs.erase(g_graphs.begin() + (long)lru);
+    }
+    GraphEntry ne;
+    ne.device = dev;
+    ne.ws = workspace;
+    ne.key = key;
+    ne.image = image;
+    ne.nout = (std::size_t)B.nout;
+    LQ_CUDA(cudaHostAlloc((void**)&ne.h_image, image > 0 ? image : 256, cudaHostAllocPortable));
+    LQ_CUDA(cudaHostAlloc((void**)&ne.h_out, sizeof(double) * (ne.nout > 0 ? ne.nout : 1),
+                          cudaHostAllocPortable));
+    cudaGraph_t graph;
+    LQ_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+    cudaMemcpyAsync(p, ne.h_image, image, cudaMemcpyHostToDevice, gs);
+    cudaMemsetAsync(A.counters, 0, sizeof(int32_t) * 2, gs);
+    batch_kernel<256><<<grid, 256, smem, gs>>>(A);
+    cudaMemcpyAsync(ne.h_out, A.out, sizeof(double) * B.nout, cudaMemcpyDeviceToHost, gs);
+    cudaError_t ce = cudaStreamEndCapture(gs, &graph);
+    if (ce == cudaSuccess) {
+      ce = cudaGraphInstantiate(&ne.exec, graph, 0);
+      cudaGraphDestroy(graph);
+    }
+    if (ce != cudaSuccess) {
+      drop_entry(ne);
+      (void)cudaGetLastError();
+      return fail(LQ_ERR_CUDA, "batch graph capture: %s", cudaGetErrorString(ce));
+    }
+    g_graphs.push_back(ne);
+    E = &g_graphs.back();
+  }
+  E->last_use = ++g_graph_clock;
+  std::size_t at = 0;
+  for (const Sec& sc : secs) {
+    if (sc.n) std::memcpy(E->h_image + at, sc.src, sc.n);
+    at += sc.cap;
+  }
+  LQ_CUDA(cudaEventRecord(g_ev_in[dev], s));
+  LQ_CUDA(cudaStreamWaitEvent(gs, g_ev_in[dev], 0));
+  LQ_CUDA(cudaGraphLaunch(E->exec, gs));
+  LQ_CUDA(cudaEventRecord(g_ev_out[dev], gs));
+  LQ_CUDA(cudaStreamWaitEvent(s, g_ev_out[dev], 0));
+  LQ_CUDA(cudaStreamSynchronize(gs));
+  out.assign(E->h_out, E->h_out + B.nout);
   return LQ_OK;
 }
 

@@ -238,6 +238,12 @@ lq_status lower_gate(const lq_gate& g, int n, double theta, Lowered& L) {
   return LQ_OK;
 }
 
+static uint64_t dbits_u(double v) {
+  uint64_t u;
+  std::memcpy(&u, &v, sizeof u);
+  return u;
+}
+
 // Merge runs of consecutive fixed dyadic diagonal ops (phases that are exact
 // multiples of 2 pi / 2^34: CP(pi/2^k), T, S, Z, CZ, ...) into one OP_DPHASE
 // when that needs fewer FP64 operations: the merged op costs at most two
@@ -288,6 +294,82 @@ void merge_dyadic(std::vector<LOp>& ops, int n) {
     i = j;
   }
   ops.swap(out);
+}
+
+// A phase op conditioned on exactly one bit (RZ, P, T, Z, S, ...).
+static bool one_bit_phase(const LOp& o, bool params) {
+  if (!(o.type == OP_PHASE || o.type == OP_SIGN || o.type == OP_MULI)) return false;
+  if (!params && !o.fixed) return false;
+  return o.cm != 0 && (o.cm & (o.cm - 1)) == 0;
+}
+
+static void phase_value(const LOp& o, double* a, double* b) {
+  if (o.type == OP_PHASE) {
+    *a = o.a;
+    *b = o.b;
+  } else if (o.type == OP_SIGN) {
+    *a = -1;
+    *b = 0;
+  } else {  // i^mode
+    const double re[4] = {1, 0, -1, 0}, im[4] = {0, 1, 0, -1};
+    *a = re[o.mode & 3];
+    *b = im[o.mode & 3];
+  }
+}
+
+void merge_linear(std::vector<LOp>& ops, int n, bool params, std::vector<int>* src,
+                  int coef_budget) {
+  std::vector<LOp> out;
+  std::vector<int> osrc;
+  out.reserve(ops.size());
+  std::size_t i = 0;
+  while (i < ops.size()) {
+    if (!one_bit_phase(ops[i], params)) {
+      if (src) osrc.push_back((*src)[i]);
+      out.push_back(ops[i++]);
+      continue;
+    }
+    std::size_t j = i;
+    while (j < ops.size() && one_bit_phase(ops[j], params)) j++;
+    double separate = 0;
+    uint64_t all = 0;
+    for (std::size_t k = i; k < j; k++) {
+      separate += op_flops(ops[k], n);
+      all |= ops[k].cm;
+    }
+    LOp m;
+    m.type = OP_LPHASE;
+    m.z = all;
+    m.fixed = true;
+    for (std::size_t k = i; k < j; k++) {
+      const double fr = m.fr * ops[k].fr - m.fi * ops[k].fi;
+      m.fi = m.fr * ops[k].fi + m.fi * ops[k].fr;
+      m.fr = fr;
+    }
+    for (std::size_t k = i; k < j; k++) {
+      double a, b;
+      phase_value(ops[k], &a, &b);
+      m.dfac.push_back(ops[k].cm);
+      m.dfac.push_back(ops[k].cv);
+      m.dfac.push_back(dbits_u(a));
+      m.dfac.push_back(dbits_u(b));
+    }
+    m.ncoef = 5 * (int)(j - i);
+    // merged: about 12 flops per amplitude plus per-tile tables
+    if (j - i >= 3 && m.ncoef <= coef_budget && 13.0 * std::ldexp(1.0, n) < separate) {
+      coef_budget -= m.ncoef;
+      out.push_back(m);
+      if (src) osrc.push_back(-1);
+    } else {
+      for (std::size_t k = i; k < j; k++) {
+        out.push_back(ops[k]);
+        if (src) osrc.push_back((*src)[k]);
+      }
+    }
+    i = j;
+  }
+  ops.swap(out);
+  if (src) src->swap(osrc);
 }
 
 // Magnitude window of the deferred scalar; outside it the magnitude is applied
@@ -355,6 +437,7 @@ double op_flops(const LOp& o, int n) {
     case OP_SCALE: return ((o.mode & 1) ? 2.0 : 6.0) * N;
     case OP_GRAD: return 4.0 * N;
     case OP_DPHASE: return 12.0 * N * frac;                // table combine + multiply
+    case OP_LPHASE: return 12.0 * N * frac;                // table combine + multiply
     default: return 0.0;                                   // sign flips, i^k, swaps
   }
 }
@@ -401,6 +484,21 @@ static void fill_dphase(double* pool, const LOp& s, uint64_t tile, const int* po
   }
 }
 
+// Factor list of an OP_LPHASE: per factor (tile-local cm | cv << 32, CTA cm,
+// CTA cv, re, im).
+static void fill_lphase(double* pool, const LOp& s, uint64_t tile, const int* pos) {
+  const std::size_t nf = s.dfac.size() / 4;
+  for (std::size_t f = 0; f < nf; f++) {
+    uint64_t cm = s.dfac[4 * f], cv = s.dfac[4 * f + 1];
+    uint64_t loc = (uint64_t)to_local(cm & tile, pos) | ((uint64_t)to_local(cv & tile, pos) << 32);
+    pool[5 * f + 0] = bitsd(loc);
+    pool[5 * f + 1] = bitsd(cm & ~tile);
+    pool[5 * f + 2] = bitsd(cv & ~tile);
+    pool[5 * f + 3] = bitsd(s.dfac[4 * f + 2]);
+    pool[5 * f + 4] = bitsd(s.dfac[4 * f + 3]);
+  }
+}
+
 static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef_at) {
   std::memset(&d, 0, sizeof d);
   d.type = s.type;
@@ -409,7 +507,8 @@ static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef
   d.b1 = s.g1 >= 0 ? (uint8_t)pos[s.g1] : (uint8_t)s.sub;
   if (s.type == OP_GRAD)
     d.cidx = (uint32_t)s.slot;
-  else if (s.type == OP_PAIR_GEN || s.type == OP_QUAD_GEN || s.type == OP_DPHASE)
+  else if (s.type == OP_PAIR_GEN || s.type == OP_QUAD_GEN || s.type == OP_DPHASE ||
+           s.type == OP_LPHASE)
     d.cidx = (uint32_t)coef_at;
   else
     d.cidx = (uint32_t)s.gate;
@@ -417,7 +516,9 @@ static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef
   d.cv_loc = to_local(s.cv & tile, pos);
   d.cm_glob = s.cm & ~tile;
   d.cv_glob = s.cv & ~tile;
-  d.x_loc = s.type == OP_DPHASE ? (uint32_t)(s.dfac.size() / 3) : to_local(s.x, pos);
+  d.x_loc = s.type == OP_DPHASE   ? (uint32_t)(s.dfac.size() / 3)
+            : s.type == OP_LPHASE ? (uint32_t)(s.dfac.size() / 4)
+                                  : to_local(s.x, pos);
   d.z_loc = to_local(s.z & tile, pos);
   d.z_glob = s.z & ~tile;
   d.a = s.a;
@@ -475,12 +576,25 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
   delete[] out.passes;
   delete[] out.op_src;
   out.passes = new PassParams[passes.size() > 0 ? passes.size() : 1];
+  out.pass_ops.clear();
   out.op_src = new int[(passes.size() > 0 ? passes.size() : 1) * MAX_OPS];
   for (std::size_t p = 0; p < passes.size(); p++) {
     Built& B = passes[p];
     // fill the tile up to k bits with the lowest unused bits (larger
     // contiguous loads, fewer tiles)
     for (int bit = 0; bit < n && popc64(B.tile) < k; bit++) B.tile |= 1ull << bit;
+    // the pass's ops in order; runs of one-bit phases merge within the pass
+    std::vector<LOp> plist;
+    std::vector<int> psrc;
+    for (int idx : B.idx) {
+      plist.push_back(ops[idx]);
+      psrc.push_back(idx);
+    }
+    {
+      int used = 0;
+      for (const LOp& l : plist) used += l.ncoef;
+      merge_linear(plist, n, opt.merge_params, &psrc, MAX_COEF - used);
+    }
     PassParams& P = out.passes[p];
     std::memset(&P.h, 0, sizeof P.h);
     P.h.n = n;
@@ -504,16 +618,19 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
     P.h.nobits = o;
     P.h.ntiles = 1ull << (n - k);
     int coef_at = 0, cnt = 0;
-    for (int idx : B.idx) {
-      fill_op(P.ops[cnt], ops[idx], B.tile, pos, coef_at);
-      if (ops[idx].type == OP_DPHASE) {
-        fill_dphase(P.coef + coef_at, ops[idx], B.tile, pos);
+    for (std::size_t q = 0; q < plist.size(); q++) {
+      const LOp& l = plist[q];
+      fill_op(P.ops[cnt], l, B.tile, pos, coef_at);
+      if (l.type == OP_DPHASE) {
+        fill_dphase(P.coef + coef_at, l, B.tile, pos);
         P.h.flags |= PF_DYADIC;
+      } else if (l.type == OP_LPHASE) {
+        fill_lphase(P.coef + coef_at, l, B.tile, pos);
+      } else {
+        for (int c = 0; c < l.ncoef; c++) P.coef[coef_at + c] = l.coef[c];
       }
-      else
-        for (int c = 0; c < ops[idx].ncoef; c++) P.coef[coef_at + c] = ops[idx].coef[c];
-      coef_at += ops[idx].ncoef;
-      out.op_src[p * MAX_OPS + cnt] = idx;
+      coef_at += l.ncoef;
+      out.op_src[p * MAX_OPS + cnt] = psrc[q];
       cnt++;
     }
     if (p + 1 == passes.size() && need_scale) {
@@ -524,9 +641,11 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
       s.b = zi;
       fill_op(P.ops[cnt], s, B.tile, pos, 0);
       out.op_src[p * MAX_OPS + cnt] = -1;
+      plist.push_back(s);
       cnt++;
     }
     P.h.nops = cnt;
+    out.pass_ops.push_back(std::move(plist));
   }
   return LQ_OK;
 }

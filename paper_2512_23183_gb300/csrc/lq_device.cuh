@@ -230,37 +230,152 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
     }
     case OP_DPHASE: {
       // E(s) = sum of the weights of the factors whose conditions hold, mod
-      // 2^34; the phase exp(2 pi i E / 2^34) = hi[E >> 17] * lo[E & (2^17-1)]
+      // 2^34; phase exp(2 pi i E / 2^34) = hi[E >> 17] * lo[E & (2^17-1)].
+      // When every factor has at most one tile bit beyond the op's common
+      // condition, E is linear in the tile bits: E = e0 + sum_b c_b s_b,
+      // evaluated per amplitude from two 7-bit partial-sum tables built per
+      // tile; otherwise each amplitude sums its factors directly.
+      __shared__ unsigned long long dp_e0, dp_c[MAX_TILE_BITS + 1];
+      __shared__ unsigned long long dp_t[2][128];
+      __shared__ int dp_nonlin;
       const int nf = (int)op.x_loc;
       const double* F = coef + op.cidx;
       const uint32_t cnt = T >> __popc(cm);
-      const uint64_t MASK = (1ull << DYADIC_BITS) - 1ull, LOMASK = (1ull << DYADIC_HALF) - 1ull;
-      uint64_t e0 = 0;   // factors decided by CTA bits alone
-      for (int f = 0; f < nf; f++) {
+      const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull, LOMASK = (1ull << DYADIC_HALF) - 1ull;
+      if (tid <= MAX_TILE_BITS) dp_c[tid] = 0;
+      if (tid == 0) {
+        dp_e0 = 0;
+        dp_nonlin = 0;
+      }
+      __syncthreads();
+      for (int f = tid; f < nf; f += BLOCK) {
         const uint64_t loc = (uint64_t)__double_as_longlong(F[4 * f]);
         const uint64_t gm = (uint64_t)__double_as_longlong(F[4 * f + 1]);
         const uint64_t gv = (uint64_t)__double_as_longlong(F[4 * f + 2]);
-        if ((uint32_t)loc == 0 && (base & gm) == gv) e0 += (uint64_t)__double_as_longlong(F[4 * f + 3]);
+        const unsigned long long w = (unsigned long long)__double_as_longlong(F[4 * f + 3]);
+        if ((base & gm) != gv) continue;                 // factor off for this tile
+        const uint32_t lm = (uint32_t)loc & ~cm, lv = (uint32_t)(loc >> 32);
+        if (lm == 0) {
+          atomicAdd(&dp_e0, w);
+        } else if ((lm & (lm - 1)) == 0) {
+          const int b = __ffs(lm) - 1;
+          if (lv & lm) {
+            atomicAdd(&dp_c[b], w);
+          } else {                                      // w (1 - s_b)
+            atomicAdd(&dp_e0, w);
+            atomicAdd(&dp_c[b], ((1ull << DYADIC_BITS) - w) & M34);
+          }
+        } else {
+          dp_nonlin = 1;
+        }
       }
+      __syncthreads();
+      if (!dp_nonlin) {
+        for (uint32_t v = tid; v < 256; v += BLOCK) {
+          const int c = v >> 7;
+          unsigned long long e = 0;
+          for (int b = 0; b < 7; b++)
+            if (((v & 127) >> b) & 1 && 7 * c + b <= MAX_TILE_BITS) e += dp_c[7 * c + b];
+          dp_t[c][v & 127] = e;
+        }
+        __syncthreads();
+        const unsigned long long e0 = dp_e0;
+        for (uint32_t j = tid; j < cnt; j += BLOCK) {
+          const uint32_t s = expand(j, cm, cv);
+          const unsigned long long e = (e0 + dp_t[0][s & 127] + dp_t[1][(s >> 7) & 127]) & M34;
+          if (e == 0) continue;
+          double2 w = dtab[e >> DYADIC_HALF];
+          const unsigned long long lo = e & LOMASK;
+          if (lo) {
+            const double2 wl = dtab[(1u << DYADIC_HALF) + lo];
+            w = cmul(w, wl.x, wl.y);
+          }
+          sm[s] = cmul(sm[s], w.x, w.y);
+        }
+      } else {
+        for (uint32_t j = tid; j < cnt; j += BLOCK) {
+          const uint32_t s = expand(j, cm, cv);
+          unsigned long long e = 0;
+          for (int f = 0; f < nf; f++) {
+            const uint64_t loc = (uint64_t)__double_as_longlong(F[4 * f]);
+            const uint64_t gm = (uint64_t)__double_as_longlong(F[4 * f + 1]);
+            const uint64_t gv = (uint64_t)__double_as_longlong(F[4 * f + 2]);
+            if ((s & (uint32_t)loc) == (uint32_t)(loc >> 32) && (base & gm) == gv)
+              e += (unsigned long long)__double_as_longlong(F[4 * f + 3]);
+          }
+          e &= M34;
+          if (e == 0) continue;
+          double2 w = dtab[e >> DYADIC_HALF];
+          const unsigned long long lo = e & LOMASK;
+          if (lo) {
+            const double2 wl = dtab[(1u << DYADIC_HALF) + lo];
+            w = cmul(w, wl.x, wl.y);
+          }
+          sm[s] = cmul(sm[s], w.x, w.y);
+        }
+      }
+      break;
+    }
+    case OP_LPHASE: {
+      // phase(s) = prod_f w_f^[cond_f(s)] with one condition bit per factor:
+      // per tile, e0 = product of the factors decided by CTA bits and, per
+      // tile bit b, c_b = product of the factors on b (a factor that needs
+      // s_b = 0 contributes w to e0 and conj(w) to c_b); then two 7-bit
+      // tables of products (built by doubling, e0 folded into the first)
+      // give phase(s) = t0[s & 127] * t1[s >> 7].
+      __shared__ double2 lp_c[MAX_TILE_BITS + 1];
+      __shared__ double2 lp_t[2][128];
+      const int nf = (int)op.x_loc;
+      const double* F = coef + op.cidx;
+      const int k = 31 - __clz(T);
+      if (tid <= (uint32_t)k) {
+        // thread b < k builds c_b; thread k builds e0
+        double cr = 1, ci = 0;
+        for (int f = 0; f < nf; f++) {
+          const uint64_t loc = (uint64_t)__double_as_longlong(F[5 * f]);
+          const uint64_t gm = (uint64_t)__double_as_longlong(F[5 * f + 1]);
+          const uint64_t gv = (uint64_t)__double_as_longlong(F[5 * f + 2]);
+          if ((base & gm) != gv) continue;
+          const uint32_t lm = (uint32_t)loc, lv = (uint32_t)(loc >> 32);
+          double wr = F[5 * f + 3], wi = F[5 * f + 4];
+          if (lm == 0) {
+            if (tid != (uint32_t)k) continue;
+          } else {
+            const int b = __ffs(lm) - 1;
+            if (tid == (uint32_t)k) {
+              if (lv & lm) continue;         // e0 takes w of the s_b = 0 factors
+            } else {
+              if (b != (int)tid) continue;
+              if (!(lv & lm)) wi = -wi;      // conj(w) on s_b = 1
+            }
+          }
+          const double nr = fma(cr, wr, -ci * wi), ni = fma(cr, wi, ci * wr);
+          cr = nr;
+          ci = ni;
+        }
+        lp_c[tid] = make_double2(cr, ci);
+      }
+      __syncthreads();
+      if (tid < 2) lp_t[tid][0] = tid == 0 ? lp_c[k] : make_double2(1.0, 0.0);
+      __syncthreads();
+      for (int r = 0; r < 7; r++) {
+        for (uint32_t v = tid; v < 2u << r; v += BLOCK) {
+          const int c = v >> r, lo = v & ((1u << r) - 1u);
+          const int b = 7 * c + r;
+          if (b < k) {
+            const double2 x = lp_t[c][lo], y = lp_c[b];
+            lp_t[c][lo | (1u << r)] = cmul(x, y.x, y.y);
+          }
+        }
+        __syncthreads();
+      }
+      const uint32_t cnt = T >> __popc(cm);
       for (uint32_t j = tid; j < cnt; j += BLOCK) {
         const uint32_t s = expand(j, cm, cv);
-        uint64_t e = e0;
-        for (int f = 0; f < nf; f++) {
-          const uint64_t loc = (uint64_t)__double_as_longlong(F[4 * f]);
-          const uint32_t lm = (uint32_t)loc, lv = (uint32_t)(loc >> 32);
-          if (lm == 0) continue;
-          const uint64_t gm = (uint64_t)__double_as_longlong(F[4 * f + 1]);
-          const uint64_t gv = (uint64_t)__double_as_longlong(F[4 * f + 2]);
-          if ((s & lm) == lv && (base & gm) == gv)
-            e += (uint64_t)__double_as_longlong(F[4 * f + 3]);
-        }
-        e &= MASK;
-        if (e == 0) continue;
-        double2 w = dtab[e >> DYADIC_HALF];
-        const uint64_t lo = e & LOMASK;
-        if (lo) {
-          const double2 wl = dtab[(1u << DYADIC_HALF) + lo];
-          w = cmul(w, wl.x, wl.y);
+        double2 w = lp_t[0][s & 127];
+        if (k > 7) {
+          const double2 w1 = lp_t[1][(s >> 7) & 127];
+          w = cmul(w, w1.x, w1.y);
         }
         sm[s] = cmul(sm[s], w.x, w.y);
       }

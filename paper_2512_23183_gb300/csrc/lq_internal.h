@@ -56,6 +56,9 @@ enum OpType : uint8_t {
   OP_DPHASE,      // merged dyadic phases: exp(2 pi i E(idx) / 2^34), E = sum of
                   // integer weights of the factors whose conditions hold
                   // (x_loc factors at coef[cidx..], 4 doubles each)
+  OP_LPHASE,      // merged one-bit phases: product of the unit factors w_f whose
+                  // single condition bit holds (x_loc factors at coef[cidx..],
+                  // 5 doubles each)
   OP_TYPE_COUNT
 };
 
@@ -157,6 +160,7 @@ struct ScheduleOptions {
   int k = 10;                // tile bits
   int m = 5;                 // contiguous low bits always in the tile
   bool force_scale = false;  // always end with a (final) OP_SCALE
+  bool merge_params = true;  // merge one-bit phases of parametrised gates too
 };
 
 // Per-state replacement of one gate's coefficients (shifted circuits of the
@@ -173,7 +177,9 @@ struct Schedule {
   int n = 0;
   int npasses = 0;
   PassParams* passes = nullptr;   // host array (npasses)
-  int* op_src = nullptr;          // npasses * MAX_OPS: index of the source LOp
+  int* op_src = nullptr;          // npasses * MAX_OPS: index of the source LOp (-1:
+                                  // synthetic or merged)
+  std::vector<std::vector<LOp>> pass_ops;   // the final ops of each pass
   Schedule() = default;
   Schedule(const Schedule&) = delete;
   Schedule& operator=(const Schedule&) = delete;
@@ -187,8 +193,12 @@ struct Schedule {
 lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, double zi,
                        const ScheduleOptions& opt, Schedule& out);
 
-// Merge runs of fixed dyadic diagonal ops into OP_DPHASE where cheaper.
+// Merge runs of fixed dyadic diagonal ops into OP_DPHASE, and runs of
+// one-bit phase ops into OP_LPHASE, where cheaper.  With params = false, ops
+// of parametrised gates are left alone (per-circuit patches address them).
 void merge_dyadic(std::vector<LOp>& ops, int n);
+void merge_linear(std::vector<LOp>& ops, int n, bool params, std::vector<int>* src,
+                  int coef_budget);
 
 // Validate and lower a whole circuit at the given parameters.  The caller
 // owns *ops_out (delete[]).  (*zr, *zi) is the product of deferred factors.
