@@ -192,10 +192,13 @@ class Step:
                                          launches=plan_g["npasses"], kernel="pass_kernel"),
             "a7_expval": dict(bytes=16 * N, flops=self._expval_flops(), launches=2,
                               kernel="expval_kernel"),
-            "a8_psr_batched_n10": dict(bytes=0.0, flops=0.0, launches=4),
+            # one persistent batch_kernel launch (graph-replayed with its copies)
+            "a8_psr_batched_n10": dict(bytes=0.0, flops=0.0, launches=1),
         }
         if self.has_adjoint:
-            self.rows["a9_adjoint_n10"] = dict(bytes=0.0, flops=0.0, launches=0)
+            ap = lq.adjoint_plan(10, self.vgates, self.vth, len(self.vterms))
+            self.rows["a9_adjoint_n10"] = dict(bytes=0.0, flops=ap["dp_flops"],
+                                               launches=ap["npasses"])
         self.bytes = sum(r["bytes"] for r in self.rows.values())
 
     def _expval_flops(self):

@@ -256,6 +256,12 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
 /* Plan of lq_qft (host only). */
 lq_status lq_qft_plan(int n, int method, lq_plan_info* out);
 
+/* Plan of lq_adjoint_grad (host only): npasses counts every kernel launch of
+ * the call (initialisation, forward passes, <H>, H psi, reverse passes,
+ * gradient reduction); dp_flops counts the forward and reverse passes. */
+lq_status lq_adjoint_plan(int n, const lq_gate* gates, int ng, const double* params, int np,
+                          int nt, lq_plan_info* out);
+
 /* ---------------------------------------------------------------------------
  * Uneven batches: many independent problems (each its own n, circuit and
  * Hamiltonian) in one persistent launch.  Problems are described by

@@ -91,7 +91,7 @@ EXPORTS = [
     "lq_batch_workspace_size", "lq_batch_param_shift", "lq_circuit_plan", "lq_qft_plan",
     "lq_expval_pauli_sum_noalloc", "lq_server_footprint", "lq_server_create",
     "lq_server_submit", "lq_server_wait", "lq_server_destroy", "lq_vqe_workspace_size",
-    "lq_vqe_adam",
+    "lq_vqe_adam", "lq_adjoint_plan",
 ]
 
 
@@ -159,6 +159,8 @@ def load(build_if_missing=True):
     L.lq_circuit_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
                                   P(LqPlanInfo)]
     L.lq_qft_plan.argtypes = [ctypes.c_int, ctypes.c_int, P(LqPlanInfo)]
+    L.lq_adjoint_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
+                                  ctypes.c_int, P(LqPlanInfo)]
     _lib = L
     return L
 
@@ -352,6 +354,15 @@ def circuit_plan(n, gates, params=None):
     p, pp, np_ = _params(params)
     info = LqPlanInfo()
     _check(load().lq_circuit_plan(n, g, len(gates), pp, np_, ctypes.byref(info)))
+    return dict(npasses=info.npasses, tile_bits=info.tile_bits, dp_flops=info.dp_flops,
+                dram_bytes=info.dram_bytes)
+
+
+def adjoint_plan(n, gates, params, nt):
+    g = pack_gates(gates)
+    p, pp, np_ = _params(params)
+    info = LqPlanInfo()
+    _check(load().lq_adjoint_plan(n, g, len(gates), pp, np_, int(nt), ctypes.byref(info)))
     return dict(npasses=info.npasses, tile_bits=info.tile_bits, dp_flops=info.dp_flops,
                 dram_bytes=info.dram_bytes)
 

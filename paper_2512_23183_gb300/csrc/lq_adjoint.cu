@@ -92,9 +92,123 @@ static LOp grad_op(const lq_gate& g, int n, double* fgen) {
 
 }  // namespace lq
 
+namespace lq {
+// The reverse sweep as scheduled tile passes: for k = L..1 an OP_GRAD op
+// (if gate k has a parameter), then the ops of U_k^dag.  factor[slot] is the
+// generator factor times |zeta|^2 at the gradient op's execution point.
+static lq_status build_sweep(int n, const lq_gate* gates, int ng, const double* params,
+                             std::vector<LOp>& ops, std::vector<double>& factor,
+                             std::vector<int>& slot_param, Schedule& S) {
+  lq_status st;
+  ops.clear();
+  factor.clear();
+  slot_param.clear();
+  ops.reserve((std::size_t)ng * 2 + 8);
+  double zr = 1, zi = 0;
+  for (int gi = ng - 1; gi >= 0; gi--) {
+    const lq_gate& G = gates[gi];
+    double th = G.angle + (G.param >= 0 ? params[G.param] : 0.0);
+    if (G.param >= 0) {
+      double fgen;
+      LOp go = grad_op(G, n, &fgen);
+      go.slot = (int)factor.size();
+      go.gate = gi;
+      go.a = fgen;   // the |zeta|^2 part is added in execution order below
+      factor.push_back(fgen);
+      slot_param.push_back(G.param);
+      ops.push_back(go);
+    }
+    lq_gate inv = inverse_gate(G);
+    Lowered L;
+    st = lower_gate(inv, n, -th, L);
+    if (st) return st;
+    for (int j = 0; j < L.nops; j++) {
+      L.op[j].gate = gi;
+      if (j == 0) {
+        L.op[j].fr = L.zr;
+        L.op[j].fi = L.zi;
+      }
+      ops.push_back(L.op[j]);
+    }
+    double nr = zr * L.zr - zi * L.zi, ni = zr * L.zi + zi * L.zr;
+    zr = nr;
+    zi = ni;
+    double mag = std::hypot(zr, zi);
+    if (mag < 1e-100 || mag > 1e100) {
+      LOp sc;
+      sc.type = OP_SCALE;
+      sc.mode = 1;
+      sc.a = mag;
+      sc.fr = 1.0 / mag;
+      ops.push_back(sc);
+      zr /= mag;
+      zi /= mag;
+    }
+  }
+  ScheduleOptions sopt;
+  st = schedule_ops(n, ops.data(), ops.size(), zr, zi, sopt, S);
+  if (st) return st;
+  // A gradient op sees the states divided by the deferred scalar accumulated
+  // over the ops executed before it; the scheduler may reorder commuting
+  // ops, so accumulate in execution order.
+  {
+    double ar = 1, ai = 0;
+    for (int ps = 0; ps < S.npasses; ps++)
+      for (const LOp& l : S.pass_ops[ps]) {
+        if (l.type == OP_GRAD) {
+          factor[l.slot] = l.a * (ar * ar + ai * ai);
+        } else if (!(l.type == OP_SCALE && (l.mode & 2))) {
+          double nr2 = ar * l.fr - ai * l.fi, ni2 = ar * l.fi + ai * l.fr;
+          ar = nr2;
+          ai = ni2;
+        }
+      }
+  }
+  return LQ_OK;
+}
+
+}  // namespace lq
+
 using namespace lq;
 
 extern "C" {
+
+lq_status lq_adjoint_plan(int n, const lq_gate* gates, int ng, const double* params, int np,
+                          int nt, lq_plan_info* out) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
+  st = check_gates(n, gates, ng, params, np);
+  if (st) return st;
+  lq_plan_info fwd;
+  st = lq_circuit_plan(n, gates, ng, params, np, &fwd);
+  if (st) return st;
+  std::vector<LOp> ops;
+  std::vector<double> factor;
+  std::vector<int> slot_param;
+  Schedule S;
+  st = build_sweep(n, gates, ng, params, ops, factor, slot_param, S);
+  if (st) return st;
+  double fl = fwd.dp_flops;
+  int rev = 0;
+  for (int p = 0; p < S.npasses; p++) {
+    int nops = S.passes[p].h.nops;
+    if (p == S.npasses - 1 && nops > 0 && S.passes[p].ops[nops - 1].type == OP_SCALE &&
+        (S.passes[p].ops[nops - 1].mode & 2))
+      nops--;
+    if (nops == 0) continue;
+    rev++;
+    for (const LOp& l : S.pass_ops[p]) fl += (l.type == OP_GRAD ? 1.0 : 2.0) * op_flops(l, n);
+  }
+  const int chunks = nt > 0 ? (nt + EXP_MAX_TERMS - 1) / EXP_MAX_TERMS : 0;
+  // init, forward passes, <H> (2 per chunk), H psi (1 per chunk), reverse
+  // passes, gradient reduction
+  out->npasses = 1 + fwd.npasses + 2 * chunks + chunks + rev + (np > 0 ? 1 : 0);
+  out->tile_bits = fwd.tile_bits;
+  out->dp_flops = fl;
+  out->dram_bytes = fwd.dram_bytes + 64.0 * std::ldexp(1.0, n) * rev;
+  return LQ_OK;
+}
 
 size_t lq_adjoint_workspace_size(int n, int ng, int np, int nt) {
   if (n < 1 || n > 34 || ng < 0 || np < 0) return 0;
@@ -154,73 +268,13 @@ lq_status lq_adjoint_grad(int n, const lq_gate* gates, int ng, const double* par
   st = lq_apply_pauli_sum(lam, psi, n, terms, nt, stream);
   if (st) return st;
 
-  // reverse sweep lowered into ops
   std::vector<LOp> ops;
-  ops.reserve((std::size_t)ng * 2 + 8);
   std::vector<double> factor;
   std::vector<int> slot_param;
-  double zr = 1, zi = 0;
-  for (int gi = ng - 1; gi >= 0; gi--) {
-    const lq_gate& G = gates[gi];
-    double th = G.angle + (G.param >= 0 ? params[G.param] : 0.0);
-    if (G.param >= 0) {
-      double fgen;
-      LOp go = grad_op(G, n, &fgen);
-      go.slot = (int)factor.size();
-      go.gate = gi;
-      go.a = fgen;   // the |zeta|^2 part is added in execution order below
-      factor.push_back(fgen);
-      slot_param.push_back(G.param);
-      ops.push_back(go);
-    }
-    lq_gate inv = inverse_gate(G);
-    Lowered L;
-    st = lower_gate(inv, n, -th, L);
-    if (st) return st;
-    for (int j = 0; j < L.nops; j++) {
-      L.op[j].gate = gi;
-      if (j == 0) {
-        L.op[j].fr = L.zr;
-        L.op[j].fi = L.zi;
-      }
-      ops.push_back(L.op[j]);
-    }
-    double nr = zr * L.zr - zi * L.zi, ni = zr * L.zi + zi * L.zr;
-    zr = nr;
-    zi = ni;
-    double mag = std::hypot(zr, zi);
-    if (mag < 1e-100 || mag > 1e100) {
-      LOp sc;
-      sc.type = OP_SCALE;
-      sc.mode = 1;
-      sc.a = mag;
-      sc.fr = 1.0 / mag;
-      ops.push_back(sc);
-      zr /= mag;
-      zi /= mag;
-    }
-  }
-  const int nslots = (int)factor.size();
-  ScheduleOptions sopt;
   Schedule S;
-  st = schedule_ops(n, ops.data(), ops.size(), zr, zi, sopt, S);
+  st = build_sweep(n, gates, ng, params, ops, factor, slot_param, S);
   if (st) return st;
-  // A gradient op sees the states divided by the deferred scalar accumulated
-  // over the ops executed before it; the scheduler may reorder commuting
-  // ops, so accumulate in execution order.
-  {
-    double ar = 1, ai = 0;
-    for (int ps = 0; ps < S.npasses; ps++)
-      for (const LOp& l : S.pass_ops[ps]) {
-        if (l.type == OP_GRAD) {
-          factor[l.slot] = l.a * (ar * ar + ai * ai);
-        } else if (!(l.type == OP_SCALE && (l.mode & 2))) {
-          double nr2 = ar * l.fr - ai * l.fi, ni2 = ar * l.fi + ai * l.fr;
-          ar = nr2;
-          ai = ni2;
-        }
-      }
-  }
+  const int nslots = (int)factor.size();
   // slots grouped by parameter, in slot order
   std::vector<int> first((std::size_t)np + 1, 0), count((std::size_t)np + 1, 0);
   std::vector<int> order;
