@@ -99,8 +99,29 @@ int build_exp_chunks(int n, const lq_pauli_term* terms, int nt, ExpParams* chunk
         T.c2 = 2.0 * P.coeff;
         T.z = P.zmask;
         T.k0 = __builtin_popcountll(P.xmask & P.zmask) & 3;
+        T.chunk = 0;
+        if (x == 0 && P.zmask) {
+          const int lo = __builtin_ctzll(P.zmask), hi = 63 - __builtin_clzll(P.zmask);
+          if (lo / EXP_CHUNK_BITS == hi / EXP_CHUNK_BITS) {
+            T.chunk = 1 + lo / EXP_CHUNK_BITS;
+            E->tables = 1;
+          }
+        }
         G.count++;
       }
+    }
+  }
+  // groups whose terms all have the same parity of Y factors need only one
+  // component of conj(psi_i) psi_j
+  for (int c = 0; c <= ci; c++) {
+    ExpParams& E = chunks[c];
+    for (int g = 0; g < E.ngroups; g++) {
+      ExpGroup& G = E.groups[g];
+      G.part = 0;
+      if (G.x == 0 || G.count == 0) continue;
+      int odd = 0, even = 0;
+      for (int t = G.first; t < G.first + G.count; t++) (E.terms[t].k0 & 1 ? odd : even)++;
+      G.part = odd == 0 ? 1 : even == 0 ? 2 : 0;
     }
   }
   return ci + 1;

@@ -54,6 +54,7 @@ struct BProb {
   int32_t n, k, npasses, pass_first;
   int32_t ngroups, group_first;
   int32_t circ_first, ncirc;
+  int32_t tables, pad2;
   int32_t np, out_first;
   int32_t comb_first, pad;
 };
@@ -91,39 +92,14 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-// <H> of one state (shared or global memory) by one block: same grouping and
-// pair formula as expval_kernel.
+// <H> of one state (shared or global memory) by one block.
 template <int BLOCK>
 __device__ double expval_block(const double2* st, int n, const ExpGroup* groups, int ngroups,
-                               const ExpTerm* terms, double* red) {
-  const uint64_t N = 1ull << n;
-  double acc = 0.0;
-  for (int g = 0; g < ngroups; g++) {
-    const ExpGroup G = groups[g];
-    if (G.x == 0) {
-      for (uint64_t i = threadIdx.x; i < N; i += BLOCK) {
-        const double2 v = st[i];
-        const double p = fma(v.x, v.x, v.y * v.y);
-        for (int t = G.first; t < G.first + G.count; t++) {
-          const uint32_t f = (uint32_t)(__popcll(i & terms[t].z) & 1) << 31;
-          acc = fma(xsign(terms[t].c, f), p, acc);
-        }
-      }
-    } else {
-      for (uint64_t j = threadIdx.x; j < (N >> 1); j += BLOCK) {
-        const uint64_t i = insert0_64(j, G.h), l = i ^ G.x;
-        const double2 a = st[i], b = st[l];
-        const double vr = fma(a.x, b.x, a.y * b.y);
-        const double vi = fma(a.x, b.y, -(a.y * b.x));
-        for (int t = G.first; t < G.first + G.count; t++) {
-          const int kk = (terms[t].k0 + 2 * (__popcll(l & terms[t].z) & 1)) & 3;
-          const double val = (kk & 1) ? vi : vr;
-          const uint32_t f = (uint32_t)(((kk + 1) & 2) >> 1) << 31;
-          acc = fma(xsign(terms[t].c2, f), val, acc);
-        }
-      }
-    }
-  }
+                               const ExpTerm* terms, double* red, double* tab, int tables) {
+  if (tables) expval_tables(tab, n, groups, ngroups, terms);
+  __syncthreads();
+  const double acc = expval_partial(st, n, groups, ngroups, terms, threadIdx.x, BLOCK,
+                                    tables ? tab : nullptr);
   return block_sum<BLOCK>(acc, red);
 }
 
@@ -155,6 +131,7 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
   extern __shared__ double2 sm[];
   __shared__ uint64_t hioff[256];
   __shared__ double red[BLOCK / 32];
+  __shared__ double etab[((34 + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS) * 256];
   __shared__ int s_item, s_last;
   double2* __restrict__ scratch = A.scratch + (uint64_t)blockIdx.x * A.scratch_stride;
   for (;;) {
@@ -182,7 +159,8 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
           __syncthreads();
         }
       }
-      e = expval_block<BLOCK>(sm, n, A.groups + P.group_first, P.ngroups, A.terms, red);
+      e = expval_block<BLOCK>(sm, n, A.groups + P.group_first, P.ngroups, A.terms, red, etab,
+                              P.tables);
     } else {
       // tile passes over the CTA's scratch state
       for (int p = 0; p < P.npasses; p++) {
@@ -212,7 +190,8 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
           __syncthreads();
         }
       }
-      e = expval_block<BLOCK>(scratch, n, A.groups + P.group_first, P.ngroups, A.terms, red);
+      e = expval_block<BLOCK>(scratch, n, A.groups + P.group_first, P.ngroups, A.terms, red,
+                              etab, P.tables);
     }
     if (threadIdx.x == 0) A.E[c] = e;
   }
@@ -418,6 +397,7 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B) {
       }
     }
     P.ngroups = (int)B.groups.size() - P.group_first;
+    for (int c = 0; c < got; c++) P.tables |= ch[c].tables;
     P.circ_first = (int)B.patches.size();
     P.ncirc = (int)hp.patches.size();
     P.np = hp.np;

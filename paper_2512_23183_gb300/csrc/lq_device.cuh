@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "lq_internal.h"
+#include "lq_kernels.h"
 
 namespace lq {
 
@@ -60,6 +61,79 @@ __device__ __forceinline__ uint64_t deposit(uint64_t v, const int8_t* pos, int c
 }
 
 // All threads of the block call it; the caller synchronises.
+// Partial <H> of one thread over state `st` (shared or global memory): the
+// thread visits amplitudes/pairs t0, t0 + nth, ...  Terms sharing an X mask
+// form a group.  A group with x != 0 visits each unordered pair (i, i^x) once
+// (i has the top bit of x clear) and adds 2 c_t Re(i^kk conj(psi_i) psi_j),
+// kk = k0 + 2 parity(j & z), j = i^x (only the Re or Im part of
+// conj(psi_i) psi_j when the group's terms allow).  The x == 0 group adds
+// c_t (-1)^popcount(i & z_t) |psi_i|^2, terms inside one 8-bit index chunk
+// through the tables `tab` (per chunk 256 entries, built by the caller;
+// nullptr: all terms direct).
+__device__ __forceinline__ double expval_partial(const double2* __restrict__ st, int n,
+                                                 const ExpGroup* __restrict__ groups,
+                                                 int ngroups, const ExpTerm* __restrict__ terms,
+                                                 uint64_t t0, uint64_t nth,
+                                                 const double* __restrict__ tab) {
+  const uint64_t N = 1ull << n;
+  const int nch = (n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS;
+  double acc = 0.0;
+  for (int g = 0; g < ngroups; g++) {
+    const ExpGroup G = groups[g];
+    if (G.x == 0) {
+      for (uint64_t i = t0; i < N; i += nth) {
+        const double2 v = st[i];
+        const double p = fma(v.x, v.x, v.y * v.y);
+        double d = 0.0;
+        if (tab)
+          for (int c = 0; c < nch; c++)
+            d += tab[c * 256 + ((i >> (EXP_CHUNK_BITS * c)) & 255)];
+        for (int t = G.first; t < G.first + G.count; t++) {
+          if (tab && terms[t].chunk > 0) continue;
+          const uint32_t f = (uint32_t)(__popcll(i & terms[t].z) & 1) << 31;
+          d += xsign(terms[t].c, f);
+        }
+        acc = fma(d, p, acc);
+      }
+    } else {
+      for (uint64_t j = t0; j < (N >> 1); j += nth) {
+        const uint64_t i = insert0_64(j, G.h), l = i ^ G.x;
+        const double2 a = st[i], b = st[l];
+        const double vr = G.part == 2 ? 0.0 : fma(a.x, b.x, a.y * b.y);
+        const double vi = G.part == 1 ? 0.0 : fma(a.x, b.y, -(a.y * b.x));
+        for (int t = G.first; t < G.first + G.count; t++) {
+          const int kk = (terms[t].k0 + 2 * (__popcll(l & terms[t].z) & 1)) & 3;
+          // Re(i^kk v): vr, -vi, -vr, vi
+          const double val = (kk & 1) ? vi : vr;
+          const uint32_t f = (uint32_t)(((kk + 1) & 2) >> 1) << 31;
+          acc = fma(xsign(terms[t].c2, f), val, acc);
+        }
+      }
+    }
+  }
+  return acc;
+}
+
+// Build the diagonal-term chunk tables (nch x 256 doubles) in shared memory:
+// tab[c][v] = sum over the x == 0 terms inside chunk c of c_t (-1)^popcount(v & z_t).
+__device__ __forceinline__ void expval_tables(double* tab, int n, const ExpGroup* groups,
+                                              int ngroups, const ExpTerm* terms) {
+  const int nch = (n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS;
+  for (int e = threadIdx.x; e < nch * 256; e += blockDim.x) {
+    const int c = e >> 8, v = e & 255;
+    double s = 0.0;
+    for (int g = 0; g < ngroups; g++) {
+      if (groups[g].x != 0) continue;
+      for (int t = groups[g].first; t < groups[g].first + groups[g].count; t++) {
+        if (terms[t].chunk != c + 1) continue;
+        const uint32_t zl = (uint32_t)(terms[t].z >> (EXP_CHUNK_BITS * c)) & 255u;
+        s += (__popc((uint32_t)v & zl) & 1) ? -terms[t].c : terms[t].c;
+      }
+    }
+    tab[e] = s;
+  }
+}
+
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
 // are `base`; dtab: dyadic phase tables (hi: 2^17 entries exp(2 pi i h / 2^17),
 // lo: 2^17 entries exp(2 pi i l / 2^34)).

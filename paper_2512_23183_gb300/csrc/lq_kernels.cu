@@ -320,38 +320,14 @@ __global__ void __launch_bounds__(BLOCK) expval_kernel(const __grid_constant__ E
                                                        const double2* __restrict__ state,
                                                        uint64_t stride,
                                                        double* __restrict__ partial) {
+  __shared__ double tab[((34 + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS) * 256];
   const double2* __restrict__ st = state + blockIdx.y * stride;
-  const uint64_t N = 1ull << E.n;
+  if (E.tables) expval_tables(tab, E.n, E.groups, E.ngroups, E.terms);
+  __syncthreads();
   const uint64_t nthreads = (uint64_t)gridDim.x * BLOCK;
   const uint64_t t0 = blockIdx.x * (uint64_t)BLOCK + threadIdx.x;
-  double acc = 0.0;
-  for (int g = 0; g < E.ngroups; g++) {
-    const ExpGroup G = E.groups[g];
-    if (G.x == 0) {
-      for (uint64_t i = t0; i < N; i += nthreads) {
-        double2 v = st[i];
-        double p = fma(v.x, v.x, v.y * v.y);
-        for (int t = G.first; t < G.first + G.count; t++) {
-          uint32_t f = (uint32_t)(__popcll(i & E.terms[t].z) & 1) << 31;
-          acc = fma(xsign(E.terms[t].c, f), p, acc);
-        }
-      }
-    } else {
-      for (uint64_t j = t0; j < (N >> 1); j += nthreads) {
-        uint64_t i = insert0_64(j, G.h), l = i ^ G.x;
-        double2 a = st[i], b = st[l];
-        double vr = fma(a.x, b.x, a.y * b.y);
-        double vi = fma(a.x, b.y, -(a.y * b.x));
-        for (int t = G.first; t < G.first + G.count; t++) {
-          int kk = (E.terms[t].k0 + 2 * (__popcll(l & E.terms[t].z) & 1)) & 3;
-          // Re(i^kk v): vr, -vi, -vr, vi
-          double val = (kk & 1) ? vi : vr;
-          uint32_t f = (uint32_t)(((kk + 1) & 2) >> 1) << 31;
-          acc = fma(xsign(E.terms[t].c2, f), val, acc);
-        }
-      }
-    }
-  }
+  double acc = expval_partial(st, E.n, E.groups, E.ngroups, E.terms, t0, nthreads,
+                              E.tables ? tab : nullptr);
   // block reduction in a fixed order
   __shared__ double red[BLOCK / 32];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);

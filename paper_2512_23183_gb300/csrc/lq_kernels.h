@@ -15,22 +15,26 @@ namespace lq {
 // ------------------------------------------------------- Pauli-sum params
 
 struct ExpTerm {
-  double c;    // coefficient
-  double c2;   // 2 * coefficient (pair form of <H>)
-  uint64_t z;  // Z mask (global bits)
-  int32_t k0;  // number of Y factors mod 4
-  int32_t pad;
+  double c;      // coefficient
+  double c2;     // 2 * coefficient (pair form of <H>)
+  uint64_t z;    // Z mask (global bits)
+  int32_t k0;    // number of Y factors mod 4
+  int32_t chunk; // diagonal terms: 1 + the 8-bit index chunk holding z (read
+                 // from a table), 0: applied directly
 };
 struct ExpGroup {
-  uint64_t x;   // common X mask
-  int32_t h;    // top bit of x (pair enumeration), 0 for x == 0
+  uint64_t x;    // common X mask
+  int32_t h;     // top bit of x (pair enumeration), 0 for x == 0
   int32_t first, count;
-  int32_t pad;
+  int32_t part;  // x != 0: 0 needs Re and Im of conj(psi_i) psi_j, 1 only Re, 2 only Im
 };
+constexpr int EXP_CHUNK_BITS = 8;  // diagonal terms inside one 8-bit chunk use a table
 constexpr int EXP_MAX_TERMS = 640;
 constexpr int EXP_MAX_GROUPS = 240;
 struct ExpParams {
   int32_t n, ngroups;
+  int32_t tables;   // nonzero: some diagonal terms are read from chunk tables
+  int32_t pad;
   ExpGroup groups[EXP_MAX_GROUPS];
   ExpTerm terms[EXP_MAX_TERMS];
 };
