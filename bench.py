@@ -202,19 +202,33 @@ class Step:
         self.bytes = sum(r["bytes"] for r in self.rows.values())
 
     def _expval_flops(self):
-        # per X group: 4 FP64 ops per pair (vr, vi) + 1 FMA per term; diagonal
-        # group: |psi|^2 + 1 FMA per term (FMA = 2 flops)
+        """FP64 flops of expval_kernel as it runs (FMA = 2): per X group and
+        pair, 3 flops per component of conj(psi_i) psi_j it needs (one when
+        all terms share the parity of their Y count) and 2 per term; per
+        amplitude of the diagonal group, 3 for |psi|^2, one add per 8-bit
+        chunk table (when some Z term fits a chunk), one per term outside
+        the tables, 2 for the final multiply-add."""
         groups = {}
         for c, s in self.terms:
             x = "".join("1" if ch in "XY" else "0" for ch in s)
-            groups[x] = groups.get(x, 0) + 1
-        N = float(1 << self.n)
+            groups.setdefault(x, []).append(s)
+        n = self.n
+        N = float(1 << n)
         fl = 0.0
-        for x, cnt in groups.items():
+        for x, ss in groups.items():
             if "1" in x:
-                fl += (N / 2) * (6 + 2 * cnt)
+                ny = {sum(ch == "Y" for ch in s) % 2 for s in ss}
+                fl += (N / 2) * ((3 if len(ny) == 1 else 6) + 2 * len(ss))
             else:
-                fl += N * (3 + 2 * cnt)
+                direct, tables = 0, False
+                for s in ss:
+                    bits = [n - 1 - q for q, ch in enumerate(s) if ch == "Z"]
+                    if bits and min(bits) // 8 == max(bits) // 8:
+                        tables = True
+                    else:
+                        direct += 1
+                nch = (n + 7) // 8 if tables else 0
+                fl += N * (3 + nch + direct + 2)
         return fl
 
     def run(self, events=None, host_in=None):
@@ -441,6 +455,48 @@ def vqe_extras(device):
     return res
 
 
+def qft_extras(device, sizes=(20, 24, 28, 30), reps=3):
+    """The QFT workload as configured: FFT form and gate form at n = 20, 24,
+    28, 30 on seeded Gaussian inputs, each timed with CUDA events (mean of
+    `reps` after a warm-up): ms, state-vector GB/s by the plan's algorithmic
+    bytes, FP64 TFLOP/s by the plan's flops."""
+    import torch
+
+    import paper_2512_23183_gb300 as lq
+
+    out = {}
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    for n in sizes:
+        g = torch.Generator(device=device)
+        g.manual_seed(1000 + n)
+        v = torch.randn(2 << n, dtype=torch.float64, device=device, generator=g)
+        psi = torch.view_as_complex(v.view(-1, 2))
+        psi /= torch.linalg.vector_norm(psi)
+        r = {}
+        for name, meth in (("fft", lq.QFT_FFT), ("gates", lq.QFT_GATES)):
+            plan = lq.qft_plan(n, meth)
+            lq.qft(psi, n, method=meth)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                lq.qft(psi, n, method=meth)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = plan["dram_bytes"] / (ms * 1e-3) / 1e9
+            tf = plan["dp_flops"] / (ms * 1e-3) / 1e12
+            r[name] = {"ms": round(ms, 3), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
+                       "fp64_tflops": round(tf, 4), "fp64_frac": round(tf / FP64_PEAK_TFLOPS, 4),
+                       "launches": plan["npasses"]}
+        out["n%d" % n] = r
+        del psi, v
+        torch.cuda.empty_cache()
+    return out
+
+
 def serve_extras(device, count=48, slots=8):
     """Serving workload: seeded request stream (n ~ U{8..28}, depth ~
     U{2..20}, 50/50 energy / energy+gradient, Heisenberg chain or random
@@ -576,6 +632,7 @@ def main():
     torch.cuda.empty_cache()
     if rank == 0:
         if not a.no_extras:
+            out["qft"] = qft_extras(device)
             out["vqe"] = vqe_extras(device)
             torch.cuda.empty_cache()
             out["serve"] = serve_extras(device)

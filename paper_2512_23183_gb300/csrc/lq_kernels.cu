@@ -75,12 +75,32 @@ const double2* dyadic_tables(cudaError_t* err) {
 // `nstates` states (stride `stride` amplitudes apart); a tile is the 2^k
 // amplitudes base | deposit(s, tbits), s < 2^k.  Tile loads and stores are
 // coalesced runs of 2^m contiguous amplitudes.
+// 16-byte asynchronous global -> shared copy (completion by
+// cp.async.wait_group, a hardware wait: no spin loop).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One CTA processes tiles w = blockIdx.x, blockIdx.x + gridDim.x, ... of the
+// `nstates` states (stride `stride` amplitudes apart); a tile is the 2^k
+// amplitudes base | deposit(s, tbits), s < 2^k.  Tile loads and stores are
+// coalesced runs of 2^m contiguous amplitudes.  With `dbuf`, the next tile
+// is loaded into a second shared buffer while the current one is computed.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ PassParams P,
-                                                     double2* __restrict__ state,
-                                                     uint64_t stride, int nstates,
-                                                     const Patch* __restrict__ patches) {
-  extern __shared__ double2 sm[];
+                                                        double2* __restrict__ state,
+                                                        uint64_t stride, int nstates,
+                                                        const Patch* __restrict__ patches,
+                                                        int dbuf) {
+  extern __shared__ double2 smem_tiles[];
   __shared__ uint64_t hioff[256];
   const int k = P.h.k, m = P.h.m, nops = P.h.nops;
   const uint32_t T = 1u << k;
@@ -90,14 +110,39 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
     hioff[j] = deposit(j, P.h.tbits + m, kh);
   const uint64_t ntiles = P.h.ntiles;
   const uint64_t total = ntiles * (uint64_t)nstates;
+  const bool zero = (P.h.flags & PF_INIT_ZERO) != 0;
+  const bool store = !(P.h.flags & PF_NO_STORE);
   __syncthreads();
-  for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
+  auto tile_of = [&](uint64_t w, uint64_t* base) -> double2* {
     const uint64_t si = w / ntiles, t = w - si * ntiles;
-    double2* __restrict__ st = state + si * stride;
-    const uint64_t base = deposit(t, P.h.obits, P.h.nobits);
-    if (P.h.flags & PF_INIT_ZERO) {
+    *base = deposit(t, P.h.obits, P.h.nobits);
+    return state + si * stride;
+  };
+  auto issue = [&](uint64_t w, double2* buf) {
+    uint64_t base;
+    const double2* st = tile_of(w, &base);
+    for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+      cp_async16(buf + s, st + (base | hioff[s >> m] | (s & lowmask)));
+    cp_async_commit();
+  };
+  uint64_t w = blockIdx.x;
+  int cur = 0;
+  if (dbuf && !zero && w < total) issue(w, smem_tiles);
+  for (; w < total; w += gridDim.x, cur ^= 1) {
+    double2* __restrict__ sm = smem_tiles + (dbuf ? cur * T : 0);
+    uint64_t base;
+    double2* __restrict__ st = tile_of(w, &base);
+    const uint64_t si = w / ntiles;
+    if (zero) {
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
         sm[s] = make_double2((base == 0 && s == 0) ? 1.0 : 0.0, 0.0);
+    } else if (dbuf) {
+      if (w + gridDim.x < total) {
+        issue(w + gridDim.x, smem_tiles + (cur ^ 1) * T);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
     } else {
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
         sm[s] = st[base | hioff[s >> m] | (s & lowmask)];
@@ -134,12 +179,13 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
         __syncthreads();
       }
     }
-    if (!(P.h.flags & PF_NO_STORE)) {
+    if (store) {
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
         st[base | hioff[s >> m] | (s & lowmask)] = sm[s];
     }
     __syncthreads();
   }
+  if (dbuf) cp_async_wait<0>();
 }
 
 static constexpr int kPassBlock = 256;
@@ -148,7 +194,10 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
                         cudaStream_t s, const Patch* patches) {
   (void)cudaGetLastError();  // report only this launcher's own errors
   static bool configured = false;
-  size_t smem = sizeof(double2) << P.h.k;
+  // double buffering when two tiles fit comfortably (k <= 11) and the pass
+  // loads from HBM
+  const int dbuf = (P.h.k <= 11 && !(P.h.flags & PF_INIT_ZERO)) ? 1 : 0;
+  size_t smem = (sizeof(double2) << P.h.k) * (dbuf ? 2 : 1);
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(pass_kernel<kPassBlock>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -157,7 +206,7 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
     configured = true;
   }
   uint64_t total = P.h.ntiles * (uint64_t)nstates;
-  int per_sm = smem <= 16384 ? 8 : smem <= 32768 ? 6 : smem <= 65536 ? 3 : 1;
+  int per_sm = smem <= 16384 ? 8 : smem <= 32768 ? 4 : smem <= 65536 ? 3 : 1;
   uint64_t cap = (uint64_t)sm_count() * per_sm;
   int grid = (int)(total < cap ? total : cap);
   if (P.h.flags & PF_DYADIC) {
@@ -167,9 +216,11 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
     static thread_local PassParams Q;   // launch copy carrying the table address
     Q = P;
     Q.h.dtab = t;
-    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(Q, state, stride, nstates, patches);
+    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(Q, state, stride, nstates, patches,
+                                                           dbuf);
   } else {
-    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, patches);
+    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, patches,
+                                                           dbuf);
   }
   return cudaGetLastError();
 }
