@@ -151,6 +151,7 @@ static lq_status run_ops(double2* states, uint64_t stride, int nstates, int n, c
                          std::size_t nops, double zr, double zi, bool init_zero,
                          cudaStream_t s) {
   ScheduleOptions opt;
+  opt.lphase_table = true;   // run by pass_kernel
   Schedule S;
   lq_status st = schedule_ops(n, ops, nops, zr, zi, opt, S);
   if (st) return st;
@@ -237,6 +238,7 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
   st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi);
   if (st) return st;
   ScheduleOptions opt;
+  opt.lphase_table = true;   // run by pass_kernel
   Schedule S;
   st = schedule_ops(n, ops, nops, zr, zi, opt, S);
   delete[] ops;

@@ -437,7 +437,8 @@ double op_flops(const LOp& o, int n) {
     case OP_SCALE: return ((o.mode & 1) ? 2.0 : 6.0) * N;
     case OP_GRAD: return 4.0 * N;
     case OP_DPHASE: return 12.0 * N * frac;                // table combine + multiply
-    case OP_LPHASE: return 12.0 * N * frac;                // table combine + multiply
+    case OP_LPHASE:                                        // (table combine +) multiply
+      return ((o.mode & LP_TABLE) ? 6.0 : 12.0) * N * frac;
     default: return 0.0;                                   // sign flips, i^k, swaps
   }
 }
@@ -626,6 +627,17 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
         P.h.flags |= PF_DYADIC;
       } else if (l.type == OP_LPHASE) {
         fill_lphase(P.coef + coef_at, l, B.tile, pos);
+        if (opt.lphase_table && k <= LTAB_MAX_BITS && !(P.h.flags & PF_LTAB)) {
+          bool local = true;   // every factor's condition on a tile bit (or none)
+          for (std::size_t f = 0; f < l.dfac.size() / 4; f++)
+            if (l.dfac[4 * f] & ~B.tile) local = false;
+          if (local) {
+            P.ops[cnt].mode |= LP_TABLE;
+            P.h.flags |= PF_LTAB;
+            P.h.ltab_op = cnt;
+            plist[q].mode |= LP_TABLE;
+          }
+        }
       } else {
         for (int c = 0; c < l.ncoef; c++) P.coef[coef_at + c] = l.coef[c];
       }

@@ -134,14 +134,164 @@ __device__ __forceinline__ void expval_tables(double* tab, int n, const ExpGroup
   }
 }
 
+// One-bit Pauli rotation with a uniform phase per side: x = 1 << h and the
+// string's Z bits inside the tile are at most h, so for a pair (s0, s1 = s0 |
+// x) the phases are w_A = i^kA (applied to psi_s1 in out_s0) and w_B = i^kB
+// (applied to psi_s0 in out_s1), the same for every pair of the tile.  The
+// powers' parities are template arguments; their signs are folded into the
+// coefficients (tangent form: out = own + c * rot(other)) or applied as sign
+// bits (cotangent form: out = a * own + sign * rot(other)), where rot is the
+// identity for an even power and multiplication by i for an odd one.  Two
+// pairs per thread and iteration: all four loads issue before any store.
+template <bool ODD>
+__device__ __forceinline__ double2 rot_fma(double c, double2 other, double2 own) {
+  return ODD ? make_double2(fma(-c, other.y, own.x), fma(c, other.x, own.y))
+             : make_double2(fma(c, other.x, own.x), fma(c, other.y, own.y));
+}
+template <bool ODD>
+__device__ __forceinline__ double2 rot_cot(double a, double2 own, double2 other, uint32_t sg) {
+  return ODD ? make_double2(fma(a, own.x, xsign(other.y, sg ^ 0x80000000u)),
+                            fma(a, own.y, xsign(other.x, sg)))
+             : make_double2(fma(a, own.x, xsign(other.x, sg)), fma(a, own.y, xsign(other.y, sg)));
+}
+template <bool ODD>
+__device__ __forceinline__ double2 rot_perm(double2 other, uint32_t sg) {
+  return ODD ? make_double2(xsign(other.y, sg ^ 0x80000000u), xsign(other.x, sg))
+             : make_double2(xsign(other.x, sg), xsign(other.y, sg));
+}
+enum RotForm { ROT_COT = 0, ROT_TAN = 1, ROT_PERM = 2 };
+template <int BLOCK, int FORM, bool OA, bool OB>
+__device__ __forceinline__ void rot1_pairs(double2* __restrict__ sm, uint32_t cnt, uint32_t M,
+                                           uint32_t cv, uint32_t x, double a, double cA,
+                                           double cB, uint32_t sA, uint32_t sB) {
+  const uint32_t tid = threadIdx.x;
+  const int h = 31 - __clz(x);
+  const bool plain = M == x;   // no tile-local condition
+  auto idx = [&](uint32_t j) { return plain ? insert0(j, h) : expand(j, M, cv); };
+  auto pair = [&](double2 A, double2 B, double2& o0, double2& o1) {
+    if (FORM == ROT_TAN) {
+      o0 = rot_fma<OA>(cA, B, A);
+      o1 = rot_fma<OB>(cB, A, B);
+    } else if (FORM == ROT_COT) {
+      o0 = rot_cot<OA>(a, A, B, sA);
+      o1 = rot_cot<OB>(a, B, A, sB);
+    } else {
+      o0 = rot_perm<OA>(B, sA);
+      o1 = rot_perm<OB>(A, sB);
+    }
+  };
+  if ((cnt & (2 * BLOCK - 1)) == 0) {
+    for (uint32_t j = tid; j < cnt; j += 2 * BLOCK) {
+      const uint32_t p0 = idx(j), q0 = idx(j + BLOCK);
+      const double2 A = sm[p0], B = sm[p0 | x], C = sm[q0], D = sm[q0 | x];
+      double2 o0, o1, o2, o3;
+      pair(A, B, o0, o1);
+      pair(C, D, o2, o3);
+      sm[p0] = o0;
+      sm[p0 | x] = o1;
+      sm[q0] = o2;
+      sm[q0 | x] = o3;
+    }
+  } else {
+    for (uint32_t j = tid; j < cnt; j += BLOCK) {
+      const uint32_t p0 = idx(j);
+      const double2 A = sm[p0], B = sm[p0 | x];
+      double2 o0, o1;
+      pair(A, B, o0, o1);
+      sm[p0] = o0;
+      sm[p0 | x] = o1;
+    }
+  }
+}
+
+// Phase table of a table-mode OP_LPHASE (every factor's condition bit is a
+// tile bit): tab[s] = product of the factors w_f whose condition holds for
+// tile index s, s < 2^k.  Per tile bit b, c_b = product of the factors on b
+// (a factor that needs s_b = 0 contributes w to the constant e0 and conj(w)
+// to c_b); then tab is built by doubling from tab[0] = e0.  All threads call
+// it; it ends with a barrier.
+template <int BLOCK>
+__device__ __forceinline__ void build_lphase_table(double2* tab, int k, const Op& op,
+                                                   const double* __restrict__ coef) {
+  __shared__ double2 lt_c[MAX_TILE_BITS + 1];
+  const uint32_t tid = threadIdx.x;
+  const int nf = (int)op.x_loc;
+  const double* F = coef + op.cidx;
+  if (tid <= (uint32_t)k) {
+    double cr = 1, ci = 0;
+    for (int f = 0; f < nf; f++) {
+      const uint64_t loc = (uint64_t)__double_as_longlong(F[5 * f]);
+      const uint32_t lm = (uint32_t)loc, lv = (uint32_t)(loc >> 32);
+      double wr = F[5 * f + 3], wi = F[5 * f + 4];
+      if (lm == 0) {
+        if (tid != (uint32_t)k) continue;
+      } else {
+        const int b = __ffs(lm) - 1;
+        if (tid == (uint32_t)k) {
+          if (lv & lm) continue;
+        } else {
+          if (b != (int)tid) continue;
+          if (!(lv & lm)) wi = -wi;
+        }
+      }
+      const double nr = fma(cr, wr, -ci * wi), ni = fma(cr, wi, ci * wr);
+      cr = nr;
+      ci = ni;
+    }
+    lt_c[tid] = make_double2(cr, ci);
+  }
+  __syncthreads();
+  if (tid == 0) tab[0] = lt_c[k];
+  __syncthreads();
+  for (int b = 0; b < k; b++) {
+    const double2 c = lt_c[b];
+    for (uint32_t s = tid; s < (1u << b); s += BLOCK) tab[s | (1u << b)] = cmul(tab[s], c.x, c.y);
+    __syncthreads();
+  }
+}
+
+// Diagonal update v <- f(s, v) of the cnt amplitudes s = expand(j, cm, cv),
+// j < cnt; U amplitudes per thread and iteration, all loaded before any is
+// stored.
+template <int BLOCK, int U, typename F>
+__device__ __forceinline__ void diag_apply(double2* __restrict__ sm, uint32_t cnt, uint32_t cm,
+                                           uint32_t cv, F f) {
+  const uint32_t tid = threadIdx.x;
+  if (cnt % (U * BLOCK) == 0) {
+    for (uint32_t j = tid; j < cnt; j += U * BLOCK) {
+      uint32_t sx[U];
+      double2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        sx[u] = cm ? expand(j + u * BLOCK, cm, cv) : j + u * BLOCK;
+        v[u] = sm[sx[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) v[u] = f(sx[u], v[u]);
+#pragma unroll
+      for (int u = 0; u < U; u++) sm[sx[u]] = v[u];
+    }
+  } else {
+    for (uint32_t j = tid; j < cnt; j += BLOCK) {
+      const uint32_t sj = expand(j, cm, cv);
+      sm[sj] = f(sj, sm[sj]);
+    }
+  }
+}
+
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
 // are `base`; dtab: dyadic phase tables (hi: 2^17 entries exp(2 pi i h / 2^17),
-// lo: 2^17 entries exp(2 pi i l / 2^34)).
+// lo: 2^17 entries exp(2 pi i l / 2^34)); ltab: the pass's per-CTA phase
+// table (table-mode OP_LPHASE), or nullptr.
 template <int BLOCK>
 __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, const Op& op,
                                          const double* __restrict__ coef, uint64_t base,
-                                         const double2* __restrict__ dtab) {
+                                         const double2* __restrict__ dtab,
+                                         const double2* __restrict__ ltab = nullptr) {
   const uint32_t tid = threadIdx.x;
+  // per-tile tables of OP_DPHASE (2 x 128 sums) or OP_LPHASE (2 x 128
+  // phases); one op at a time uses it
+  __shared__ __align__(16) double2 op_tab[2][128];
   if ((base & op.cm_glob) != op.cv_glob) return;  // CTA-level condition
   const int zs = __popcll(base & op.z_glob) & 1;
   const uint32_t cm = op.cm_loc, cv = op.cv_loc;
@@ -153,6 +303,32 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       const double a = op.a, b = op.b;
       const uint32_t M = cm | (1u << h);
       const uint32_t cnt = T >> __popc(M);
+      if ((x & (x - 1)) == 0 && (z & ~x) == 0 && pm != PM_GEN) {
+        // uniform phases: w_A = i^kA (pairs' s1 has the Z bit), w_B = i^kB
+        const int kA = (k0 + 2 * (((z != 0) + zs) & 1)) & 3;
+        const int kB = (k0 + 2 * (zs & 1)) & 3;
+        const double cA = (kA & 2) ? -a : a, cB = (kB & 2) ? -a : a;
+        const uint32_t sA = (uint32_t)(kA & 2) << 30, sB = (uint32_t)(kB & 2) << 30;
+        const int v = ((kA & 1) << 1) | (kB & 1);
+#define LQ_ROT1(F, A_, B_) rot1_pairs<BLOCK, F, A_, B_>(sm, cnt, M, cv, x, a, cA, cB, sA, sB)
+#define LQ_ROT1_FORM(F)                      \
+  switch (v) {                               \
+    case 0: LQ_ROT1(F, false, false); break; \
+    case 1: LQ_ROT1(F, false, true); break;  \
+    case 2: LQ_ROT1(F, true, false); break;  \
+    default: LQ_ROT1(F, true, true); break;  \
+  }
+        if (pm == PM_TAN) {
+          LQ_ROT1_FORM(ROT_TAN)
+        } else if (pm == PM_COT) {
+          LQ_ROT1_FORM(ROT_COT)
+        } else {
+          LQ_ROT1_FORM(ROT_PERM)
+        }
+#undef LQ_ROT1_FORM
+#undef LQ_ROT1
+        break;
+      }
       for (uint32_t j = tid; j < cnt; j += BLOCK) {
         const uint32_t s0 = expand(j, M, cv);
         const uint32_t s1 = s0 ^ x;
@@ -181,14 +357,27 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
     }
     case OP_H: {
       const int bb = op.b0;
-      const uint32_t M = cm | (1u << bb);
+      const uint32_t xb = 1u << bb;
+      const uint32_t M = cm | xb;
       const uint32_t cnt = T >> __popc(M);
-      for (uint32_t j = tid; j < cnt; j += BLOCK) {
-        const uint32_t s0 = expand(j, M, cv);
-        const uint32_t s1 = s0 | (1u << bb);
-        double2 A = sm[s0], B = sm[s1];
-        sm[s0] = make_double2(A.x + B.x, A.y + B.y);
-        sm[s1] = make_double2(A.x - B.x, A.y - B.y);
+      if ((cnt & (2 * BLOCK - 1)) == 0) {
+        for (uint32_t j = tid; j < cnt; j += 2 * BLOCK) {
+          const uint32_t p0 = cm ? expand(j, M, cv) : insert0(j, bb);
+          const uint32_t q0 = cm ? expand(j + BLOCK, M, cv) : insert0(j + BLOCK, bb);
+          const double2 A = sm[p0], B = sm[p0 | xb], C = sm[q0], D = sm[q0 | xb];
+          sm[p0] = make_double2(A.x + B.x, A.y + B.y);
+          sm[p0 | xb] = make_double2(A.x - B.x, A.y - B.y);
+          sm[q0] = make_double2(C.x + D.x, C.y + D.y);
+          sm[q0 | xb] = make_double2(C.x - D.x, C.y - D.y);
+        }
+      } else {
+        for (uint32_t j = tid; j < cnt; j += BLOCK) {
+          const uint32_t s0 = expand(j, M, cv);
+          const uint32_t s1 = s0 | xb;
+          double2 A = sm[s0], B = sm[s1];
+          sm[s0] = make_double2(A.x + B.x, A.y + B.y);
+          sm[s1] = make_double2(A.x - B.x, A.y - B.y);
+        }
       }
       break;
     }
@@ -253,29 +442,20 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
     }
     case OP_PHASE: {
       const double wr = op.a, wi = op.b;
-      const uint32_t cnt = T >> __popc(cm);
-      for (uint32_t j = tid; j < cnt; j += BLOCK) {
-        const uint32_t s = expand(j, cm, cv);
-        sm[s] = cmul(sm[s], wr, wi);
-      }
+      diag_apply<BLOCK, 2>(sm, T >> __popc(cm), cm, cv,
+                           [&](uint32_t, double2 v) { return cmul(v, wr, wi); });
       break;
     }
     case OP_SIGN: {
-      const uint32_t cnt = T >> __popc(cm);
-      for (uint32_t j = tid; j < cnt; j += BLOCK) {
-        const uint32_t s = expand(j, cm, cv);
-        const double2 v = sm[s];
-        sm[s] = make_double2(xsign(v.x, 0x80000000u), xsign(v.y, 0x80000000u));
-      }
+      diag_apply<BLOCK, 2>(sm, T >> __popc(cm), cm, cv, [&](uint32_t, double2 v) {
+        return make_double2(xsign(v.x, 0x80000000u), xsign(v.y, 0x80000000u));
+      });
       break;
     }
     case OP_MULI: {
       const int kk = op.mode & 3;
-      const uint32_t cnt = T >> __popc(cm);
-      for (uint32_t j = tid; j < cnt; j += BLOCK) {
-        const uint32_t s = expand(j, cm, cv);
-        sm[s] = mul_ipow(sm[s], kk);
-      }
+      diag_apply<BLOCK, 2>(sm, T >> __popc(cm), cm, cv,
+                           [&](uint32_t, double2 v) { return mul_ipow(v, kk); });
       break;
     }
     case OP_PARITY: {
@@ -310,7 +490,7 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       // evaluated per amplitude from two 7-bit partial-sum tables built per
       // tile; otherwise each amplitude sums its factors directly.
       __shared__ unsigned long long dp_e0, dp_c[MAX_TILE_BITS + 1];
-      __shared__ unsigned long long dp_t[2][128];
+      unsigned long long(*dp_t)[128] = reinterpret_cast<unsigned long long(*)[128]>(op_tab);
       __shared__ int dp_nonlin;
       const int nf = (int)op.x_loc;
       const double* F = coef + op.cidx;
@@ -391,6 +571,13 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       break;
     }
     case OP_LPHASE: {
+      if ((op.mode & LP_TABLE) && ltab) {
+        diag_apply<BLOCK, 4>(sm, T >> __popc(cm), cm, cv, [&](uint32_t s, double2 v) {
+          const double2 w = ltab[s];
+          return cmul(v, w.x, w.y);
+        });
+        break;
+      }
       // phase(s) = prod_f w_f^[cond_f(s)] with one condition bit per factor:
       // per tile, e0 = product of the factors decided by CTA bits and, per
       // tile bit b, c_b = product of the factors on b (a factor that needs
@@ -398,7 +585,7 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       // tables of products (built by doubling, e0 folded into the first)
       // give phase(s) = t0[s & 127] * t1[s >> 7].
       __shared__ double2 lp_c[MAX_TILE_BITS + 1];
-      __shared__ double2 lp_t[2][128];
+      double2(*lp_t)[128] = op_tab;
       const int nf = (int)op.x_loc;
       const double* F = coef + op.cidx;
       const int k = 31 - __clz(T);
@@ -458,12 +645,10 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
     case OP_SCALE: {
       const double wr = op.a, wi = op.b;
       if (op.mode & 1) {
-        for (uint32_t s = tid; s < T; s += BLOCK) {
-          double2 v = sm[s];
-          sm[s] = make_double2(v.x * wr, v.y * wr);
-        }
+        diag_apply<BLOCK, 4>(sm, T, 0, 0,
+                             [&](uint32_t, double2 v) { return make_double2(v.x * wr, v.y * wr); });
       } else {
-        for (uint32_t s = tid; s < T; s += BLOCK) sm[s] = cmul(sm[s], wr, wi);
+        diag_apply<BLOCK, 4>(sm, T, 0, 0, [&](uint32_t, double2 v) { return cmul(v, wr, wi); });
       }
       break;
     }

@@ -102,6 +102,8 @@ struct PassHeader {
   int32_t n, k, m, nops;
   int32_t nobits;
   int32_t flags;          // PF_* below
+  int32_t ltab_op;        // PF_LTAB: index of the table-mode OP_LPHASE
+  int32_t reserved;
   uint64_t ntiles;        // 2^(n-k)
   const void* dtab;       // dyadic phase tables (device), set at launch
   int8_t tbits[16];       // tile-local bit j -> global bit position
@@ -111,7 +113,15 @@ enum PassFlags : int32_t {
   PF_INIT_ZERO = 1,       // do not load: start from |0...0> (whole-state tile)
   PF_NO_STORE = 2,        // do not store the tile back
   PF_DYADIC = 4,          // the pass has OP_DPHASE ops (needs dtab)
+  PF_LTAB = 8,            // ops[ltab_op] is a table-mode OP_LPHASE: its 2^k-entry
+                          // phase table is built once per CTA (pass_kernel only)
 };
+
+// OP_LPHASE in table mode (Op::mode bit): every factor's condition bit is a
+// tile bit, so phase(s) is the same for every tile and one 2^k-entry table,
+// built once per CTA, gives it with one complex multiply per amplitude.
+constexpr uint8_t LP_TABLE = 0x80;
+constexpr int LTAB_MAX_BITS = 10;   // table-mode tiles: 2^10 entries, 16 KiB
 
 struct PassParams {
   PassHeader h;
@@ -161,6 +171,8 @@ struct ScheduleOptions {
   int m = 5;                 // contiguous low bits always in the tile
   bool force_scale = false;  // always end with a (final) OP_SCALE
   bool merge_params = true;  // merge one-bit phases of parametrised gates too
+  bool lphase_table = false; // mark one OP_LPHASE per pass for a per-CTA table
+                             // (schedules run by pass_kernel only)
 };
 
 // Per-state replacement of one gate's coefficients (shifted circuits of the

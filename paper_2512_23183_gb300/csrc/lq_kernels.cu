@@ -71,10 +71,6 @@ const double2* dyadic_tables(cudaError_t* err) {
 
 // ----------------------------------------------------------- tile passes
 
-// One CTA processes tiles w = blockIdx.x, blockIdx.x + gridDim.x, ... of the
-// `nstates` states (stride `stride` amplitudes apart); a tile is the 2^k
-// amplitudes base | deposit(s, tbits), s < 2^k.  Tile loads and stores are
-// coalesced runs of 2^m contiguous amplitudes.
 // 16-byte asynchronous global -> shared copy (completion by
 // cp.async.wait_group, a hardware wait: no spin loop).
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -92,22 +88,30 @@ __device__ __forceinline__ void cp_async_wait() {
 // One CTA processes tiles w = blockIdx.x, blockIdx.x + gridDim.x, ... of the
 // `nstates` states (stride `stride` amplitudes apart); a tile is the 2^k
 // amplitudes base | deposit(s, tbits), s < 2^k.  Tile loads and stores are
-// coalesced runs of 2^m contiguous amplitudes.  With `dbuf`, the next tile
-// is loaded into a second shared buffer while the current one is computed.
+// coalesced runs of 2^m contiguous amplitudes.  With `dbuf`, the next tile is
+// copied into a second buffer (cp.async) while the current one is computed,
+// so the CTAs of an SM do not all wait on HBM at the same time.  With
+// PF_LTAB, the phase table of the pass's table-mode OP_LPHASE (every factor
+// on a tile bit) is built once per CTA, after the tile buffers, and serves
+// every tile.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ PassParams P,
                                                         double2* __restrict__ state,
-                                                        uint64_t stride, int nstates,
-                                                        const Patch* __restrict__ patches,
-                                                        int dbuf) {
+                                                        uint64_t stride, int nstates, int dbuf) {
   extern __shared__ double2 smem_tiles[];
-  __shared__ uint64_t hioff[256];
+  __shared__ uint32_t hioff[256];   // high tile bits' global offsets >> m
   const int k = P.h.k, m = P.h.m, nops = P.h.nops;
   const uint32_t T = 1u << k;
   const uint32_t lowmask = (1u << m) - 1u;
   const int kh = k - m;
   for (uint32_t j = threadIdx.x; j < (1u << kh); j += BLOCK)
-    hioff[j] = deposit(j, P.h.tbits + m, kh);
+    hioff[j] = (uint32_t)(deposit(j, P.h.tbits + m, kh) >> m);
+  const double2* ltab = nullptr;
+  if (P.h.flags & PF_LTAB) {
+    double2* t = smem_tiles + (dbuf ? 2 * T : T);
+    build_lphase_table<BLOCK>(t, k, P.ops[P.h.ltab_op], P.coef);
+    ltab = t;
+  }
   const uint64_t ntiles = P.h.ntiles;
   const uint64_t total = ntiles * (uint64_t)nstates;
   const bool zero = (P.h.flags & PF_INIT_ZERO) != 0;
@@ -122,17 +126,15 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
     uint64_t base;
     const double2* st = tile_of(w, &base);
     for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
-      cp_async16(buf + s, st + (base | hioff[s >> m] | (s & lowmask)));
+      cp_async16(buf + s, st + (base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)));
     cp_async_commit();
   };
-  uint64_t w = blockIdx.x;
   int cur = 0;
-  if (dbuf && !zero && w < total) issue(w, smem_tiles);
-  for (; w < total; w += gridDim.x, cur ^= 1) {
+  if (dbuf && blockIdx.x < total) issue(blockIdx.x, smem_tiles);
+  for (uint64_t w = blockIdx.x; w < total; w += gridDim.x, cur ^= 1) {
     double2* __restrict__ sm = smem_tiles + (dbuf ? cur * T : 0);
     uint64_t base;
     double2* __restrict__ st = tile_of(w, &base);
-    const uint64_t si = w / ntiles;
     if (zero) {
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
         sm[s] = make_double2((base == 0 && s == 0) ? 1.0 : 0.0, 0.0);
@@ -145,43 +147,16 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
       }
     } else {
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
-        sm[s] = st[base | hioff[s >> m] | (s & lowmask)];
+        sm[s] = st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)];
     }
     __syncthreads();
-    if (patches == nullptr) {
-      for (int o = 0; o < nops; o++) {
-        apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab);
-        __syncthreads();
-      }
-    } else {
-      // shifted circuit: replace the coefficients of the patched gate's ops
-      // and multiply the final scale by the ratio of deferred factors
-      const Patch pt = patches[si];
-      for (int o = 0; o < nops; o++) {
-        Op op = P.ops[o];
-        if ((int)op.cidx == pt.gate &&
-            (op.type == OP_PAULI || op.type == OP_PHASE || op.type == OP_PARITY)) {
-          if (op.b1 == 0) {
-            op.a = pt.a0;
-            op.b = pt.b0;
-            if (op.type == OP_PAULI) op.mode = (uint8_t)((op.mode & ~3) | pt.mode0);
-          } else {
-            op.a = pt.a1;
-            op.b = pt.b1;
-          }
-        } else if (op.type == OP_SCALE && (op.mode & 2)) {
-          const double ar = op.a, ai = op.b;
-          op.a = ar * pt.zr - ai * pt.zi;
-          op.b = ar * pt.zi + ai * pt.zr;
-          op.mode &= ~1;
-        }
-        apply_op<BLOCK>(sm, T, op, P.coef, base, (const double2*)P.h.dtab);
-        __syncthreads();
-      }
+    for (int o = 0; o < nops; o++) {
+      apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab, ltab);
+      __syncthreads();
     }
     if (store) {
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
-        st[base | hioff[s >> m] | (s & lowmask)] = sm[s];
+        st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)] = sm[s];
     }
     __syncthreads();
   }
@@ -191,13 +166,13 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
 static constexpr int kPassBlock = 256;
 
 cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, int nstates,
-                        cudaStream_t s, const Patch* patches) {
+                        cudaStream_t s) {
   (void)cudaGetLastError();  // report only this launcher's own errors
   static bool configured = false;
-  // double buffering when two tiles fit comfortably (k <= 11) and the pass
-  // loads from HBM
+  const size_t tile = sizeof(double2) << P.h.k;
+  // double buffering for passes that load from HBM with tiles of <= 2^11
   const int dbuf = (P.h.k <= 11 && !(P.h.flags & PF_INIT_ZERO)) ? 1 : 0;
-  size_t smem = (sizeof(double2) << P.h.k) * (dbuf ? 2 : 1);
+  const size_t smem = tile * ((dbuf ? 2 : 1) + ((P.h.flags & PF_LTAB) ? 1 : 0));
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(pass_kernel<kPassBlock>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -206,7 +181,10 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
     configured = true;
   }
   uint64_t total = P.h.ntiles * (uint64_t)nstates;
-  int per_sm = smem <= 16384 ? 8 : smem <= 32768 ? 4 : smem <= 65536 ? 3 : 1;
+  // resident CTAs per SM: the launch bound allows 4; shared memory (dynamic
+  // + ~6 KiB static + 1 KiB reserved, of 228 KiB) may allow fewer
+  int per_sm = (int)((228u << 10) / (smem + (7u << 10)));
+  per_sm = per_sm < 1 ? 1 : per_sm > 4 ? 4 : per_sm;
   uint64_t cap = (uint64_t)sm_count() * per_sm;
   int grid = (int)(total < cap ? total : cap);
   if (P.h.flags & PF_DYADIC) {
@@ -216,11 +194,9 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
     static thread_local PassParams Q;   // launch copy carrying the table address
     Q = P;
     Q.h.dtab = t;
-    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(Q, state, stride, nstates, patches,
-                                                           dbuf);
+    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(Q, state, stride, nstates, dbuf);
   } else {
-    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, patches,
-                                                           dbuf);
+    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, dbuf);
   }
   return cudaGetLastError();
 }

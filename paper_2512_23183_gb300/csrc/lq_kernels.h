@@ -84,7 +84,7 @@ int expval_grid(int n);
 
 cudaError_t launch_init_basis(double2* amps, int n, uint64_t basis, cudaStream_t s);
 cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, int nstates,
-                        cudaStream_t s, const Patch* patches = nullptr);
+                        cudaStream_t s);
 int pass2_grid(int n, int k);
 cudaError_t launch_pass2(const PassParams& P, double2* psi, double2* lam, double* partial,
                          int grid, cudaStream_t s);

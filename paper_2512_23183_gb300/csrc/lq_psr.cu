@@ -248,6 +248,7 @@ lq_status lq_trotter_evolve(void* amps, int n, const lq_pauli_term* terms, int n
     for (int f = 0; f < nf; f++) push(field[f], h * field[f].coeff * dt);
   }
   ScheduleOptions opt;
+  opt.lphase_table = true;   // run by pass_kernel
   Schedule S;
   st = schedule_ops(n, ops.data(), ops.size(), zr, zi, opt, S);
   if (st) return st;
