@@ -34,8 +34,12 @@ namespace lq {
 constexpr int FFT_MAX_D = 12;                     // qubits per pass
 constexpr int FFT_TABLE = (1 << FFT_MAX_D) - 1;   // sum_{r<12} 2^r entries
 
-// g_tw[(1 << r) - 1 + v] = (scale, ratio) of exp(2 pi i u / 2^{r+1}) for the
-// stage with r in-tile higher qubits, stored at v = bit-reverse_r(u).
+// g_tw[(1 << r) - 1 + v]: twiddle w = exp(2 pi i u / 2^{r+1}) = exp(i pi u /
+// 2^r) of the stage with r in-tile higher qubits, u = bit-reverse_r(v), as
+// (scale, sigma): tangent form (scale c, sigma = -s/c) when the top two bits of
+// u are equal (angle in [0, pi/4) or [3pi/4, pi), |sigma| <= 1), otherwise
+// cotangent form (scale s, sigma = c/s).  The top bits of u are the low bits
+// of v, so the form is cot(v) = (v ^ (v >> 1)) & 1.
 __device__ double2 g_tw[FFT_TABLE];
 
 __global__ void fft_table_kernel() {
@@ -45,10 +49,9 @@ __global__ void fft_table_kernel() {
   int v = idx + 1 - (1 << r);
   int u = r ? (int)(__brev((unsigned)v) >> (32 - r)) : 0;
   double s, c;
-  // angle 2 pi u / 2^{r+1} = pi * (u / 2^r)
   sincospi((double)u / (double)(1 << r), &s, &c);
-  bool cot = (8 * u > (2 << r)) && (8 * u < 3 * (2 << r));
-  g_tw[idx] = cot ? make_double2(s, c / s) : make_double2(c, s / c);
+  const bool cot = ((v ^ (v >> 1)) & 1) != 0;
+  g_tw[idx] = cot ? make_double2(s, c / s) : make_double2(c, -s / c);
 }
 
 cudaError_t fft_tables_init(cudaStream_t s) {
@@ -69,9 +72,28 @@ struct FftParams {
   double scale;   // folded into the diagonal (or applied alone)
 };
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) fft_pass_kernel(const FftParams F,
-                                                         double2* __restrict__ state) {
+// Scaled radix-2 butterfly (a, b) -> (a + w b, a - w b), w = scale (1 + i
+// sigma) applied to b (tangent form) or to i b (cotangent form; -i b for the
+// inverse, whose twiddles are conjugated): with (p, q) = b or +-i b,
+// b' = (p + sigma q, q - sigma p) and out = a +- scale b' -- 6 FP64 FMAs, no
+// branch.  fpos/fneg: sign masks (inverse: flip sigma and pick -i b).
+__device__ __forceinline__ void fft_bfly(double2& a, double2& b, double2 w, uint32_t v,
+                                         uint32_t fpos, uint32_t fneg) {
+  const bool cot = ((v ^ (v >> 1)) & 1u) != 0;
+  const double p = cot ? xsign(b.y, fneg) : b.x;
+  const double q = cot ? xsign(b.x, fpos) : b.y;
+  const double sg = xsign(w.y, fpos);
+  const double tr = fma(sg, q, p), ti = fma(-sg, p, q);
+  b = make_double2(fma(-w.x, tr, a.x), fma(-w.x, ti, a.y));
+  a = make_double2(fma(w.x, tr, a.x), fma(w.x, ti, a.y));
+}
+
+// One pass of the FFT form over the d qubits [q0, q1) (tile: those bits plus
+// ms spectator low bits).  Two butterflies per thread and iteration, all four
+// loads before any store.
+template <int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F,
+                                                               double2* __restrict__ state) {
   extern __shared__ double2 sm[];
   __shared__ double2 omega[FFT_MAX_D];
   const int k = F.k, ms = F.ms, d = F.d, plo = F.plo;
@@ -81,6 +103,7 @@ __global__ void __launch_bounds__(BLOCK) fft_pass_kernel(const FftParams F,
   const int nlow = plo - ms;               // CTA bits below the group: [ms, plo)
   // sign flips for the inverse transform (conjugate twiddles), integer only
   const uint32_t fpos = F.inverse ? 0x80000000u : 0u, fneg = fpos ^ 0x80000000u;
+  const uint32_t tid = threadIdx.x;
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     // CTA bits: low part -> [ms, plo), high part -> [plo + d, n)
     const uint64_t tlo = t & ((1ull << nlow) - 1ull), thi = t >> nlow;
@@ -93,23 +116,25 @@ __global__ void __launch_bounds__(BLOCK) fft_pass_kernel(const FftParams F,
       // D(V) = scale * exp(sgn 2 pi i mout V / 2^{q1}), built by doubling from
       // directly evaluated factors exp(sgn 2 pi i (mout 2^r mod 2^{q1}) / 2^{q1})
       const uint64_t modmask = (F.q1 >= 64) ? ~0ull : ((1ull << F.q1) - 1ull);
-      if (threadIdx.x < (uint32_t)d) {
-        const uint64_t e = (mout << threadIdx.x) & modmask;
-        double s, c;
-        sincospi(2.0 * (double)e / (double)(1ull << F.q1), &s, &c);
-        omega[threadIdx.x] = make_double2(c, xsign(s, fpos));
+      if (tid < (uint32_t)d) {
+        const uint64_t e = (mout << tid) & modmask;
+        double sn, cs;
+        sincospi(2.0 * (double)e / (double)(1ull << F.q1), &sn, &cs);
+        omega[tid] = make_double2(cs, xsign(sn, fpos));
       }
-      if (threadIdx.x == 0) dtab[0] = make_double2(F.scale, 0.0);
+      if (tid == 0) dtab[0] = make_double2(F.scale, 0.0);
       __syncthreads();
       for (int r = 0; r < d; r++) {
         const double2 om = omega[r];
-        for (uint32_t v = threadIdx.x; v < (1u << r); v += BLOCK)
+        for (uint32_t v = tid; v < (1u << r); v += BLOCK)
           dtab[v | (1u << r)] = cmul(dtab[v], om.x, om.y);
         __syncthreads();
       }
     }
-    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
-      const uint64_t g = base | (s & ((1u << ms) - 1u)) | ((uint64_t)(s >> ms) << plo);
+    const uint32_t lm = (1u << ms) - 1u;
+#pragma unroll 4
+    for (uint32_t s = tid; s < T; s += BLOCK) {
+      const uint64_t g = base | (s & lm) | ((uint64_t)(s >> ms) << plo);
       double2 v = state[g];
       if (diag) {
         const double2 w = dtab[s >> ms];
@@ -118,58 +143,71 @@ __global__ void __launch_bounds__(BLOCK) fft_pass_kernel(const FftParams F,
       sm[s] = v;
     }
     __syncthreads();
-    // stages: qubit j = q0 + r acts on local bit lp = ms + d - 1 - r
-    for (int r = 0; r < d; r++) {
-      const int lp = ms + d - 1 - r;
-      const double2* tw = g_tw + ((1 << r) - 1);
-      for (uint32_t j = threadIdx.x; j < (T >> 1); j += BLOCK) {
-        const uint32_t s0 = insert0(j, lp), s1 = s0 | (1u << lp);
-        const double2 a = sm[s0], b = sm[s1];
-        double2 o0, o1;
-        if (r == 0) {
-          o0 = make_double2(a.x + b.x, a.y + b.y);
-          o1 = make_double2(a.x - b.x, a.y - b.y);
-        } else {
-          const uint32_t v = s0 >> (lp + 1);
-          const double2 w = tw[v];
-          const uint32_t u = __brev(v) >> (32 - r);
-          const bool cot = (8u * u > (2u << r)) && (8u * u < 3u * (2u << r));
-          double tr, ti;
-          if (!cot) {  // w = c (1 + i t): b' = b + i t b
-            const double tt = xsign(w.y, fpos);
-            tr = fma(-tt, b.y, b.x);
-            ti = fma(tt, b.x, b.y);
-          } else {     // w = s (u + i): b' = u b + i b
-            tr = fma(w.y, b.x, xsign(b.y, fneg));
-            ti = fma(w.y, b.y, xsign(b.x, fpos));
-          }
-          o0 = make_double2(fma(w.x, tr, a.x), fma(w.x, ti, a.y));
-          o1 = make_double2(fma(-w.x, tr, a.x), fma(-w.x, ti, a.y));
-        }
-        sm[s0] = o0;
-        sm[s1] = o1;
+    // stage r: qubit q0 + r acts on local bit lp = ms + d - 1 - r
+    {
+      const int lp = ms + d - 1;
+      const uint32_t L = 1u << lp;
+      for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
+        const uint32_t s0 = insert0(j, lp);
+        const double2 a = sm[s0], b = sm[s0 | L];
+        sm[s0] = make_double2(a.x + b.x, a.y + b.y);
+        sm[s0 | L] = make_double2(a.x - b.x, a.y - b.y);
       }
       __syncthreads();
     }
-    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
-      const uint64_t g = base | (s & ((1u << ms) - 1u)) | ((uint64_t)(s >> ms) << plo);
+    for (int r = 1; r < d; r++) {
+      const int lp = ms + d - 1 - r;
+      const uint32_t L = 1u << lp;
+      const double2* tw = g_tw + ((1 << r) - 1);
+      if (((T >> 1) & (2 * BLOCK - 1)) == 0) {
+        for (uint32_t j = tid; j < (T >> 1); j += 2 * BLOCK) {
+          const uint32_t p0 = insert0(j, lp), p1 = insert0(j + BLOCK, lp);
+          double2 a0 = sm[p0], b0 = sm[p0 | L], a1 = sm[p1], b1 = sm[p1 | L];
+          const uint32_t v0 = p0 >> (lp + 1), v1 = p1 >> (lp + 1);
+          fft_bfly(a0, b0, tw[v0], v0, fpos, fneg);
+          fft_bfly(a1, b1, tw[v1], v1, fpos, fneg);
+          sm[p0] = a0;
+          sm[p0 | L] = b0;
+          sm[p1] = a1;
+          sm[p1 | L] = b1;
+        }
+      } else {
+        for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
+          const uint32_t p0 = insert0(j, lp);
+          double2 a0 = sm[p0], b0 = sm[p0 | L];
+          const uint32_t v0 = p0 >> (lp + 1);
+          fft_bfly(a0, b0, tw[v0], v0, fpos, fneg);
+          sm[p0] = a0;
+          sm[p0 | L] = b0;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll 4
+    for (uint32_t s = tid; s < T; s += BLOCK) {
+      const uint64_t g = base | (s & lm) | ((uint64_t)(s >> ms) << plo);
       state[g] = sm[s];
     }
     __syncthreads();
   }
 }
 
-static constexpr int kFftBlock = 256;
-
+// Threads per CTA: CTAs per SM by shared memory (228 KiB), then threads so
+// that the SM holds 1024 of them (64 registers each).
 cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, double scale,
                             cudaStream_t s) {
   (void)cudaGetLastError();  // report only this launcher's own errors
   static bool configured = false;
+  const int max_smem = (int)((sizeof(double2) << MAX_TILE_BITS) + (sizeof(double2) << FFT_MAX_D));
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<kFftBlock>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((sizeof(double2) << MAX_TILE_BITS) +
-                                               (sizeof(double2) << FFT_MAX_D)));
+    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<256, 4>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fft_pass_kernel<512, 2>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fft_pass_kernel<1024, 1>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -184,11 +222,21 @@ cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, 
   F.inverse = inverse;
   F.scale = scale;
   size_t smem = (sizeof(double2) << F.k) + (sizeof(double2) << F.d);
+  int per_sm = (int)((228u << 10) / (smem + (2u << 10)));
+  per_sm = per_sm < 1 ? 1 : per_sm > 4 ? 4 : per_sm;
+  if (per_sm == 3) per_sm = 2;
+  const uint32_t T = 1u << F.k;
   uint64_t ntiles = 1ull << (n - F.k);
-  int per_sm = smem <= 16384 ? 6 : smem <= 32768 ? 4 : smem <= 65536 ? 2 : 1;
   uint64_t cap = (uint64_t)sm_count() * per_sm;
   int grid = (int)(ntiles < cap ? ntiles : cap);
-  fft_pass_kernel<kFftBlock><<<grid, kFftBlock, smem, s>>>(F, state);
+  // small tiles take the smallest block
+  if (per_sm >= 4 || T < 4096) {
+    fft_pass_kernel<256, 4><<<grid, 256, smem, s>>>(F, state);
+  } else if (per_sm == 2) {
+    fft_pass_kernel<512, 2><<<grid, 512, smem, s>>>(F, state);
+  } else {
+    fft_pass_kernel<1024, 1><<<grid, 1024, smem, s>>>(F, state);
+  }
   return cudaGetLastError();
 }
 
