@@ -12,9 +12,12 @@ One step runs every row of the hot path once:
       problem (161 circuits in shared memory)
   a9  adjoint energy + gradient of the same VQE problem (when built)
 on an n-qubit complex128 state (default n = 30: 16 GiB, inputs larger than L2,
-so no flush is needed).  `value` is the step's algorithmic state-vector bytes
-(32 B per amplitude per pass, 16 B per amplitude for <H>) divided by the step
-time measured with CUDA events; `e2e` is the same step through the library's
+so no flush is needed).  `value` is the step's state-vector DRAM bytes as the
+library's plans give them (32 B per amplitude per tile pass, 16 B per amplitude
+per read-only <H> pass; ncu confirms the kernels move exactly these) divided by
+the step time measured with CUDA events.  Fewer passes for the same work lower
+this figure while the step gets faster, so `ms_per_step` is the figure to
+compare between versions.  `e2e` is the same step through the library's
 public API with the input state copied from pinned host memory and the energy
 read back inside the timed region.
 
@@ -163,6 +166,9 @@ class Step:
         self.layer, P = W.hea(n, 1, "ladder")
         self.theta = W.angles(P, 2000 + n)
         self.terms = W.heisenberg(n)
+        # schedule autotuning of the layer (set-up, untimed): apply_circuit then
+        # uses the chosen tile width / low bits / phase-table option
+        self.tune = lq.autotune(n, self.layer, self.theta, scratch=self.work)
         self.exp_ws = torch.empty(lq.load().lq_expval_workspace_size(n, len(self.terms)),
                                   dtype=torch.uint8, device=device)
         self.e_dev = torch.zeros(1, dtype=torch.float64, device=device)
@@ -181,6 +187,7 @@ class Step:
         plan_l = lq.circuit_plan(n, self.layer, self.theta)
         plan_f = lq.qft_plan(n, lq.QFT_FFT)
         plan_g = lq.qft_plan(n, lq.QFT_GATES)
+        plan_e = lq.expval_plan(n, self.terms)
         N = float(1 << n)
         self.rows = {
             "a1_init": dict(bytes=32 * N, flops=0.0, launches=0),
@@ -190,8 +197,9 @@ class Step:
                                launches=plan_f["npasses"], kernel="fft_pass_kernel"),
             "a6_qft_gates_inverse": dict(bytes=plan_g["dram_bytes"], flops=plan_g["dp_flops"],
                                          launches=plan_g["npasses"], kernel="pass_kernel"),
-            "a7_expval": dict(bytes=16 * N, flops=self._expval_flops(), launches=2,
-                              kernel="expval_kernel"),
+            # tiled <H>: the state is read once per tile pass of X-mask groups
+            "a7_expval": dict(bytes=plan_e["dram_bytes"], flops=plan_e["dp_flops"],
+                              launches=2, kernel="expval_tile_kernel"),
             # one persistent batch_kernel launch (graph-replayed with its copies)
             "a8_psr_batched_n10": dict(bytes=0.0, flops=0.0, launches=1),
         }
@@ -200,36 +208,6 @@ class Step:
             self.rows["a9_adjoint_n10"] = dict(bytes=0.0, flops=ap["dp_flops"],
                                                launches=ap["npasses"])
         self.bytes = sum(r["bytes"] for r in self.rows.values())
-
-    def _expval_flops(self):
-        """FP64 flops of expval_kernel as it runs (FMA = 2): per X group and
-        pair, 3 flops per component of conj(psi_i) psi_j it needs (one when
-        all terms share the parity of their Y count) and 2 per term; per
-        amplitude of the diagonal group, 3 for |psi|^2, one add per 8-bit
-        chunk table (when some Z term fits a chunk), one per term outside
-        the tables, 2 for the final multiply-add."""
-        groups = {}
-        for c, s in self.terms:
-            x = "".join("1" if ch in "XY" else "0" for ch in s)
-            groups.setdefault(x, []).append(s)
-        n = self.n
-        N = float(1 << n)
-        fl = 0.0
-        for x, ss in groups.items():
-            if "1" in x:
-                ny = {sum(ch == "Y" for ch in s) % 2 for s in ss}
-                fl += (N / 2) * ((3 if len(ny) == 1 else 6) + 2 * len(ss))
-            else:
-                direct, tables = 0, False
-                for s in ss:
-                    bits = [n - 1 - q for q, ch in enumerate(s) if ch == "Z"]
-                    if bits and min(bits) // 8 == max(bits) // 8:
-                        tables = True
-                    else:
-                        direct += 1
-                nch = (n + 7) // 8 if tables else 0
-                fl += N * (3 + nch + direct + 2)
-        return fl
 
     def run(self, events=None, host_in=None):
         """One step; `events` (list of CUDA events, len 8) marks the rows.
@@ -377,6 +355,7 @@ def bench_lq(a, rank, world, device):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "hbm_frac": round(value / hbm_peak, 4),
         "rows": rows, "kernels": kernels, "roofline": roofline,
+        "autotune_hea_layer": step.tune,
         "gpu_launches": launches * a.steps,
         "clocks": clk,
     }
@@ -413,8 +392,9 @@ def e2e(step, a):
 # ------------------------------------------------------- side measurements
 
 def vqe_extras(device):
-    """Gradients per second, plain (per-circuit library calls) vs batched,
-    on the n=10 depth-4 ladder problem and the n=16 depth-8 ring problem."""
+    """Gradients per second, plain (per-circuit library calls) vs batched vs
+    adjoint, on the n=10 depth-4 ladder problem and the n=16 depth-8 ring
+    problem; the adjoint on the n=24 depth-10 problem."""
     import torch
 
     import paper_2512_23183_gb300 as lq
@@ -452,6 +432,42 @@ def vqe_extras(device):
             pass
         r["circuits_per_grad"] = 2 * len(th) + 1
         res[name] = r
+    # adjoint workload: n=24, depth-10 ladder, 480 angles (seed 5), open chain.
+    # A parameter-shift gradient here is 961 full circuits; its rate is given
+    # from the measured time of one circuit (|0..0> -> <H>), labelled as such.
+    n = 24
+    gates, P = W.hea(n, 10, "ladder")
+    th = W.angles(P, 5)
+    terms = W.heisenberg(n)
+    r = {}
+    lq.adjoint_grad(n, gates, th, terms, device=device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        lq.adjoint_grad(n, gates, th, terms, device=device)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / 3
+    r["adjoint"] = {"grads_per_s": round(1.0 / dt, 3), "ms": round(dt * 1e3, 3)}
+    psi = lq.new_state(n)
+    ws = torch.empty(lq.load().lq_expval_workspace_size(n, len(terms)), dtype=torch.uint8,
+                     device=device)
+
+    def circuit():
+        lq.state_init(psi, n)
+        lq.apply_circuit(psi, n, gates, th)
+        return lq.expval_pauli_sum(psi, n, terms, workspace=ws)
+
+    circuit()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        circuit()
+    dt1 = (time.perf_counter() - t0) / 3
+    r["one_circuit_ms"] = round(dt1 * 1e3, 3)
+    r["psr_grads_per_s_from_one_circuit"] = round(1.0 / (dt1 * (2 * P + 1)), 4)
+    r["circuits_per_grad"] = 2 * P + 1
+    res["adjoint_n24_d10_480p"] = r
+    del psi, ws
     return res
 
 
@@ -573,7 +589,7 @@ def oracle_sample_rate(n):
 
     N = float(1 << n)
     byts = (32 * N + lq.circuit_plan(n, layer, th)["dram_bytes"] + lq.qft_plan(n, 0)["dram_bytes"]
-            + lq.qft_plan(n, 1)["dram_bytes"] + 16 * N)
+            + lq.qft_plan(n, 1)["dram_bytes"] + lq.expval_plan(n, terms)["dram_bytes"])
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     del e, np
     return byts / dt / 1e9, dt, threads

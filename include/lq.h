@@ -256,6 +256,42 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
 /* Plan of lq_qft (host only). */
 lq_status lq_qft_plan(int n, int method, lq_plan_info* out);
 
+/* ---------------------------------------------------------------------------
+ * Schedule autotuner (no counterpart in the paper, whose CPU library has no
+ * tile schedule).  lq_autotune_circuit times the tile-pass schedules of
+ * lq_apply_circuit for this circuit over tile width k (9..12, at most n),
+ * contiguous low bits m (5, 6) and the per-CTA phase table (on, off), on the
+ * caller's scratch state `scratch` (device, 2^n double2, overwritten; the
+ * call synchronises `stream`), and records the fastest in a process-wide
+ * cache keyed by (GPU name and SM count, n, circuit structure: gate kinds,
+ * qubits, which gates take parameters, fixed angles).  lq_apply_circuit and
+ * lq_circuit_plan then use the recorded schedule for every circuit of that
+ * structure, whatever its parameter values.  The cache is saved to / loaded
+ * from a text file (one entry per line); lq_tune_cache_load merges entries
+ * and fails with LQ_ERR_INVALID_ARG (cache unchanged) on a malformed line.
+ */
+typedef struct {
+  int32_t tile_bits;    /* chosen k */
+  int32_t low_bits;     /* chosen m */
+  int32_t phase_table;  /* chosen per-CTA phase-table option (0/1) */
+  int32_t candidates;   /* schedules timed */
+  double ms;            /* best time (ms, min of two timed runs) */
+  double ms_default;    /* time of the default schedule (k = 10, m = 5, table on) */
+} lq_tune_result;
+
+lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng,
+                              const double* params, int np, lq_tune_result* out,
+                              lq_stream stream);
+lq_status lq_tune_cache_save(const char* path);
+lq_status lq_tune_cache_load(const char* path);
+lq_status lq_tune_cache_clear(void);
+int lq_tune_cache_size(void);
+
+/* Plan of lq_expval_pauli_sum for this term list (host only): npasses counts
+ * the reads of the state (tile passes of the tiled kernel, plus one per X-mask
+ * group evaluated by the untiled kernel); dram_bytes = 16 * 2^n per read. */
+lq_status lq_expval_plan(int n, const lq_pauli_term* terms, int nt, lq_plan_info* out);
+
 /* Plan of lq_adjoint_grad (host only): npasses counts every kernel launch of
  * the call (initialisation, forward passes, <H>, H psi, reverse passes,
  * gradient reduction); dp_flops counts the forward and reverse passes. */

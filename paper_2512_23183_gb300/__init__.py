@@ -33,6 +33,12 @@ class LqPauliTerm(ctypes.Structure):
     _fields_ = [("coeff", c_double), ("xmask", c_uint64), ("zmask", c_uint64)]
 
 
+class LqTuneResult(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_int32), ("low_bits", ctypes.c_int32),
+                ("phase_table", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("ms", c_double), ("ms_default", c_double)]
+
+
 class LqPlanInfo(ctypes.Structure):
     _fields_ = [("npasses", c_int32), ("tile_bits", c_int32), ("dp_flops", c_double),
                 ("dram_bytes", c_double)]
@@ -91,7 +97,8 @@ EXPORTS = [
     "lq_batch_workspace_size", "lq_batch_param_shift", "lq_circuit_plan", "lq_qft_plan",
     "lq_expval_pauli_sum_noalloc", "lq_server_footprint", "lq_server_create",
     "lq_server_submit", "lq_server_wait", "lq_server_destroy", "lq_vqe_workspace_size",
-    "lq_vqe_adam", "lq_adjoint_plan",
+    "lq_vqe_adam", "lq_adjoint_plan", "lq_expval_plan", "lq_autotune_circuit",
+    "lq_tune_cache_save", "lq_tune_cache_load", "lq_tune_cache_clear", "lq_tune_cache_size",
 ]
 
 
@@ -159,6 +166,14 @@ def load(build_if_missing=True):
     L.lq_circuit_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
                                   P(LqPlanInfo)]
     L.lq_qft_plan.argtypes = [ctypes.c_int, ctypes.c_int, P(LqPlanInfo)]
+    L.lq_expval_plan.argtypes = [ctypes.c_int, P(LqPauliTerm), ctypes.c_int, P(LqPlanInfo)]
+    L.lq_autotune_circuit.argtypes = [c_void_p, ctypes.c_int, P(LqGate), ctypes.c_int,
+                                      P(c_double), ctypes.c_int, P(LqTuneResult), c_void_p]
+    L.lq_tune_cache_save.argtypes = [ctypes.c_char_p]
+    L.lq_tune_cache_load.argtypes = [ctypes.c_char_p]
+    L.lq_tune_cache_clear.argtypes = []
+    L.lq_tune_cache_size.argtypes = []
+    L.lq_tune_cache_size.restype = ctypes.c_int
     L.lq_adjoint_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
                                   ctypes.c_int, P(LqPlanInfo)]
     _lib = L
@@ -363,6 +378,47 @@ def adjoint_plan(n, gates, params, nt):
     p, pp, np_ = _params(params)
     info = LqPlanInfo()
     _check(load().lq_adjoint_plan(n, g, len(gates), pp, np_, int(nt), ctypes.byref(info)))
+    return dict(npasses=info.npasses, tile_bits=info.tile_bits, dp_flops=info.dp_flops,
+                dram_bytes=info.dram_bytes)
+
+
+def autotune(n, gates, params=None, scratch=None, stream=None):
+    """Time the tile schedules of apply_circuit for this circuit on a scratch
+    state (allocated when not given) and record the fastest for every circuit
+    of the same structure on this GPU; returns the choice and its timing."""
+    if scratch is None:
+        scratch = new_state(n)
+    _check_state(scratch, n)
+    g = pack_gates(gates)
+    p, pp, np_ = _params(params)
+    r = LqTuneResult()
+    _check(load().lq_autotune_circuit(_ptr(scratch), n, g, len(gates), pp, np_, ctypes.byref(r),
+                                      _stream(stream)))
+    return dict(tile_bits=r.tile_bits, low_bits=r.low_bits, phase_table=r.phase_table,
+                candidates=r.candidates, ms=r.ms, ms_default=r.ms_default)
+
+
+def tune_cache_save(path):
+    _check(load().lq_tune_cache_save(os.fsencode(path)))
+
+
+def tune_cache_load(path):
+    _check(load().lq_tune_cache_load(os.fsencode(path)))
+
+
+def tune_cache_clear():
+    _check(load().lq_tune_cache_clear())
+
+
+def tune_cache_size():
+    return int(load().lq_tune_cache_size())
+
+
+def expval_plan(n, terms):
+    """dict(npasses, tile_bits, dp_flops, dram_bytes) of lq_expval_pauli_sum."""
+    pt = pack_terms(terms, n)
+    info = LqPlanInfo()
+    _check(load().lq_expval_plan(n, pt, len(terms), ctypes.byref(info)))
     return dict(npasses=info.npasses, tile_bits=info.tile_bits, dp_flops=info.dp_flops,
                 dram_bytes=info.dram_bytes)
 

@@ -127,6 +127,23 @@ int build_exp_chunks(int n, const lq_pauli_term* terms, int nt, ExpParams* chunk
   return ci + 1;
 }
 
+// The tiled <H> plans of a term list: 2^12 tiles (3 CTAs/SM) when class-mode
+// groups (2 FMAs per pair, little integer work) dominate, 2^11 tiles (4
+// CTAs/SM) when table-mode groups (parity index per pair) do -- measured on
+// the XYZ chain and on random 50-term sums at n = 28, 30.
+static int plan_expval_tiled(int n, const lq_pauli_term* terms, int nt,
+                             std::vector<XPlan>& xp, std::vector<lq_pauli_term>& wide) {
+  int r = build_xplans(n, terms, nt, 12, xp, wide);
+  int ncls = 0, ntab = 0;
+  for (const XPlan& X : xp)
+    for (int g = 0; g < X.ngroups; g++) {
+      ncls += X.groups[g].mode == XG_CLASS;
+      ntab += X.groups[g].mode == XG_TABLE;
+    }
+  if (r >= 0 && ntab > ncls) r = build_xplans(n, terms, nt, 11, xp, wide);
+  return r;
+}
+
 // <H> of nstates states (stride apart) into out_dev[0..nstates).  partial:
 // expval_grid(n) * nstates doubles.
 lq_status expval_states(const double2* states, uint64_t stride, int nstates, int n,
@@ -136,12 +153,29 @@ lq_status expval_states(const double2* states, uint64_t stride, int nstates, int
     LQ_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(double) * nstates, s));
     return LQ_OK;
   }
+  bool acc = false;
+  std::vector<lq_pauli_term> wide;
+  if (n >= kTiledExpvalMinN) {   // tiled passes: each tile read once per pass of groups
+    std::vector<XPlan> xp;
+    if (plan_expval_tiled(n, terms, nt, xp, wide) < 0)
+      return fail(LQ_ERR_INVALID_ARG, "internal: term plan");
+    for (std::size_t c = 0; c < xp.size(); c++) {
+      LQ_CUDA(launch_expval_tiled(xp[c], states, stride, nstates, partial, out_dev, acc, s));
+      acc = true;
+    }
+    if (wide.empty()) {
+      if (!acc) LQ_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(double) * nstates, s));
+      return LQ_OK;
+    }
+    terms = wide.data();   // X masks wider than a tile: the untiled kernel
+    nt = (int)wide.size();
+  }
   int nch = exp_chunk_count(terms, nt);
   std::vector<ExpParams> ch((std::size_t)nch);
   int got = build_exp_chunks(n, terms, nt, ch.data(), nch);
   if (got < 0) return fail(LQ_ERR_INVALID_ARG, "internal: term chunking");
   for (int c = 0; c < got; c++)
-    LQ_CUDA(launch_expval(ch[c], states, stride, nstates, partial, out_dev, c > 0, s));
+    LQ_CUDA(launch_expval(ch[c], states, stride, nstates, partial, out_dev, acc || c > 0, s));
   return LQ_OK;
 }
 
@@ -149,9 +183,10 @@ lq_status expval_states(const double2* states, uint64_t stride, int nstates, int
 // for a |0...0> start.
 static lq_status run_ops(double2* states, uint64_t stride, int nstates, int n, const LOp* ops,
                          std::size_t nops, double zr, double zi, bool init_zero,
-                         cudaStream_t s) {
+                         cudaStream_t s, const ScheduleOptions* tuned = nullptr) {
   ScheduleOptions opt;
   opt.lphase_table = true;   // run by pass_kernel
+  if (tuned) opt = *tuned;
   Schedule S;
   lq_status st = schedule_ops(n, ops, nops, zr, zi, opt, S);
   if (st) return st;
@@ -222,9 +257,60 @@ lq_status lq_apply_circuit(void* amps, int n, const lq_gate* gates, int ng,
   double zr, zi;
   st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi);
   if (st) return st;
-  st = run_ops((double2*)amps, 0, 1, n, ops, nops, zr, zi, false, (cudaStream_t)stream);
+  // the autotuner's choice for this (GPU, n, circuit structure), if any
+  ScheduleOptions tuned;
+  tuned.lphase_table = true;
+  const bool has = tuned_options(n, gates, ng, &tuned);
+  st = run_ops((double2*)amps, 0, 1, n, ops, nops, zr, zi, false, (cudaStream_t)stream,
+               has ? &tuned : nullptr);
   delete[] ops;
   return st;
+}
+
+lq_status lq_expval_plan(int n, const lq_pauli_term* terms, int nt, lq_plan_info* out) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
+  st = check_terms(n, terms, nt);
+  if (st) return st;
+  const double N = std::ldexp(1.0, n);
+  std::vector<lq_pauli_term> rest(terms, terms + nt);
+  int reads = 0, tb = 0;
+  double fl = 0;
+  if (n >= kTiledExpvalMinN && nt > 0) {
+    std::vector<XPlan> xp;
+    if (plan_expval_tiled(n, terms, nt, xp, rest) < 0)
+      return fail(LQ_ERR_INVALID_ARG, "internal: term plan");
+    for (const XPlan& X : xp) {
+      reads += X.npass;
+      const int nch = (n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS;
+      for (int g = 0; g < X.ngroups; g++) {
+        const XGroup& G = X.groups[g];
+        const int parts = G.part == 0 ? 2 : 1;
+        if (G.mode == XG_CLASS) {
+          fl += 2.0 * parts * N;                  // 2 FMA per pair and part
+        } else if (G.mode == XG_TABLE) {
+          fl += 2.5 * parts * N;                  // MUL + FMA, then FMA, per pair and part
+        } else {
+          const int direct = X.tables ? G.first + G.count - G.direct : G.count;
+          fl += (5.0 + (X.tables ? nch : 0) + direct) * N;   // |psi|^2, d(i), FMA
+        }
+      }
+      if (X.npass) tb = X.passes[0].k;
+    }
+  }
+  // untiled kernel: one read of the state per X-mask group
+  std::map<uint64_t, int> groups;
+  for (const lq_pauli_term& t : rest) groups[t.xmask]++;
+  for (auto& kv : groups) {
+    reads++;
+    fl += kv.first ? (3.0 + kv.second) * N : (3.0 + 2.0 * kv.second) * N;
+  }
+  out->npasses = reads;
+  out->tile_bits = tb;
+  out->dp_flops = fl;
+  out->dram_bytes = 16.0 * N * reads;
+  return LQ_OK;
 }
 
 lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* params, int np,
@@ -239,6 +325,7 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
   if (st) return st;
   ScheduleOptions opt;
   opt.lphase_table = true;   // run by pass_kernel
+  tuned_options(n, gates, ng, &opt);   // the schedule lq_apply_circuit would use
   Schedule S;
   st = schedule_ops(n, ops, nops, zr, zi, opt, S);
   delete[] ops;

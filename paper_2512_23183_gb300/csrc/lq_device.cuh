@@ -30,6 +30,20 @@ __device__ __forceinline__ double2 cmul(double2 v, double wr, double wi) {
   return make_double2(fma(v.x, wr, -v.y * wi), fma(v.x, wi, v.y * wr));
 }
 
+// 16-byte asynchronous global -> shared copy (completion by
+// cp.async.wait_group, a hardware wait: no spin loop).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Insert a zero bit at position b of j.
 __device__ __forceinline__ uint32_t insert0(uint32_t j, int b) {
   uint32_t lo = j & ((1u << b) - 1u);

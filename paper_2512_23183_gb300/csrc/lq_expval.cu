@@ -1,0 +1,481 @@
+// lq_expval.cu -- tiled Pauli-sum expectation value E = sum_t c_t <psi|P_t|psi>
+// (Sec. V, the observable of Eq. expval; Sec. VI's Hamiltonians) for large
+// states.
+//
+// P_t |i> = i^{k0} (-1)^{popcount(i & z)} |i ^ x> (x: X and Y sites, z: Z and
+// Y sites, k0 = number of Y factors), so a term with x != 0 pairs amplitude i
+// with j = i ^ x and contributes 2 c_t Re(i^kk conj(psi_i) psi_j) per
+// unordered pair (i has the top bit of x clear), kk = k0 + 2 parity(j & z);
+// a diagonal term (x = 0) contributes c_t (-1)^{popcount(i & z)} |psi_i|^2.
+//
+// Terms are grouped by x.  The state is read in tile passes: a pass loads
+// each 2^k-amplitude tile (bit set = the low m bits and bits covering the x
+// masks of the pass's groups) into shared memory once, and every group of the
+// pass is evaluated on the tile's pairs.  A group's per-pair coefficient
+// depends on the parities of j & z_t:
+//   * class mode (every z_t inside x, w = |x| <= 3 bits): the coefficient is
+//     a function of the pair's lower x bits ("class", 2^{w-1} of them);
+//     threads are split by class, each accumulates sum Re / Im of
+//     conj(psi_i) psi_j over its pairs (2 FP64 FMAs per pair and part) and
+//     folds its class coefficient in once per tile;
+//   * table mode (up to 4 terms): the parities index a host-built table of
+//     (coefficient of Re, coefficient of Im), one FMA per pair and part;
+//   * the diagonal group sums |psi_i|^2 d(i) with d from per-CTA 8-bit chunk
+//     tables over the global index (terms spanning chunks: directly).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "lq_device.cuh"
+#include "lq_internal.h"
+#include "lq_kernels.h"
+
+namespace lq {
+
+// ------------------------------------------------------------ host plan
+
+static uint32_t xp_to_local(uint64_t mask, const int* pos) {
+  uint32_t r = 0;
+  while (mask) {
+    const int b = __builtin_ctzll(mask);
+    mask &= mask - 1;
+    r |= 1u << pos[b];
+  }
+  return r;
+}
+
+static int pc64(uint64_t v) { return __builtin_popcountll(v); }
+
+int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<XPlan>& out,
+                 std::vector<lq_pauli_term>& wide) {
+  out.clear();
+  wide.clear();
+  if (kt > XP_TILE_BITS) kt = XP_TILE_BITS;
+  const int k = n < kt ? n : kt;
+  const int m0 = n < 5 ? n : 5;
+  const uint64_t low = (1ull << m0) - 1ull;
+
+  // groups by X mask; groups with x != 0 that cannot use class mode are split
+  // into table-mode groups of <= XP_TABLE_TERMS terms
+  struct HG {
+    uint64_t x;
+    std::vector<int> t;
+    int mode;
+  };
+  std::map<uint64_t, std::vector<int>> byx;
+  for (int t = 0; t < nt; t++) byx[terms[t].xmask].push_back(t);
+  std::vector<HG> groups;
+  HG diag{0, {}, XG_DIAG};
+  for (auto& kv : byx) {
+    if (kv.first == 0) {
+      diag.t = kv.second;
+      continue;
+    }
+    if (pc64(kv.first | low) > k) {   // X mask wider than a tile: untiled kernel
+      for (int t : kv.second) wide.push_back(terms[t]);
+      continue;
+    }
+    bool cls = pc64(kv.first) <= 3;
+    for (int t : kv.second)
+      if (terms[t].zmask & ~kv.first) cls = false;
+    if (cls) {
+      groups.push_back(HG{kv.first, kv.second, XG_CLASS});
+    } else {
+      for (std::size_t a = 0; a < kv.second.size(); a += XP_TABLE_TERMS) {
+        HG g{kv.first, {}, XG_TABLE};
+        for (std::size_t b = a; b < kv.second.size() && b < a + XP_TABLE_TERMS; b++)
+          g.t.push_back(kv.second[b]);
+        groups.push_back(g);
+      }
+    }
+  }
+  // passes: greedy, groups in ascending x
+  struct HP {
+    uint64_t tile;
+    std::vector<int> g;   // indices into groups; -1 = the diagonal group
+  };
+  std::vector<HP> passes;
+  std::vector<int> pending;
+  for (int g = 0; g < (int)groups.size(); g++) pending.push_back(g);
+  if (!diag.t.empty()) passes.push_back(HP{low, {-1}});
+  while (!pending.empty()) {
+    HP P{low, {}};
+    if (passes.size() == 1 && passes[0].g.size() == 1 && passes[0].g[0] == -1) {
+      P = passes[0];   // the diagonal group shares the first pass
+      passes.clear();
+    }
+    std::vector<int> rest;
+    for (int g : pending) {
+      const uint64_t t = P.tile | groups[g].x;
+      if (pc64(t) <= k) {
+        P.tile = t;
+        P.g.push_back(g);
+      } else {
+        rest.push_back(g);
+      }
+    }
+    if (P.g.empty()) return -1;   // cannot happen: every group fits a tile with the low bits
+    passes.push_back(P);
+    pending.swap(rest);
+  }
+
+  // fill XPlan chunks
+  auto fresh = [&]() {
+    out.emplace_back();
+    XPlan& X = out.back();
+    std::memset(&X, 0, sizeof X);
+    X.n = n;
+    X.diag = -1;
+    return &out.back();
+  };
+  XPlan* X = fresh();
+  for (const HP& P : passes) {
+    // capacity of this pass: groups, terms and coefficients
+    int ng = 0, ntm = 0, nco = 0;
+    for (int g : P.g) {
+      const HG& G = g < 0 ? diag : groups[g];
+      ng++;
+      ntm += (int)G.t.size();
+      if (G.mode == XG_CLASS) nco += 1 << (pc64(G.x) - 1);
+      if (G.mode == XG_TABLE) nco += 1 << G.t.size();
+    }
+    if (ng > XP_MAX_GROUPS || ntm > XP_MAX_TERMS || nco > XP_MAX_COEF) return -1;
+    if (X->npass == XP_MAX_PASS || X->ngroups + ng > XP_MAX_GROUPS ||
+        X->nterms + ntm > XP_MAX_TERMS || X->ncoef + nco > XP_MAX_COEF)
+      X = fresh();
+    XPass& Q = X->passes[X->npass++];
+    uint64_t tile = P.tile;
+    for (int bit = 0; bit < n && pc64(tile) < k; bit++) tile |= 1ull << bit;
+    int pos[64];
+    for (int i = 0; i < 64; i++) pos[i] = -1;
+    int j = 0, o = 0;
+    for (int bit = 0; bit < n; bit++) {
+      if (tile >> bit & 1) {
+        Q.tbits[j] = (int8_t)bit;
+        pos[bit] = j++;
+      } else {
+        Q.obits[o++] = (int8_t)bit;
+      }
+    }
+    int mm = 0;
+    while (mm < k && Q.tbits[mm] == mm) mm++;
+    Q.k = k;
+    Q.m = mm;
+    Q.nobits = o;
+    Q.g0 = X->ngroups;
+    for (int g : P.g) {
+      const HG& G = g < 0 ? diag : groups[g];
+      XGroup& D = X->groups[X->ngroups++];
+      D.mode = (int8_t)G.mode;
+      D.x = xp_to_local(G.x, pos);
+      D.h = (int8_t)(G.x ? 31 - __builtin_clz(D.x) : 0);
+      D.w = (int8_t)pc64(G.x);
+      D.first = (int16_t)X->nterms;
+      D.count = (int16_t)G.t.size();
+      // diagonal group: terms inside one 8-bit index chunk (read from the
+      // chunk tables) first, then the terms evaluated directly
+      auto in_chunk = [&](int t) {
+        const uint64_t z = terms[t].zmask;
+        if (!z) return false;
+        return __builtin_ctzll(z) / EXP_CHUNK_BITS == (63 - __builtin_clzll(z)) / EXP_CHUNK_BITS;
+      };
+      std::vector<int> order(G.t);
+      if (G.mode == XG_DIAG)
+        std::stable_partition(order.begin(), order.end(), in_chunk);
+      D.direct = D.first;
+      int odd = 0, even = 0;
+      for (int t : order) {
+        XTerm& T = X->terms[X->nterms++];
+        const lq_pauli_term& src = terms[t];
+        T.c = G.mode == XG_DIAG ? src.coeff : 2.0 * src.coeff;
+        if (G.mode == XG_DIAG) {   // diagonal terms: the full global Z mask
+          T.zl = 0;
+          T.zg = src.zmask;
+        } else {
+          T.zl = xp_to_local(src.zmask & tile, pos);
+          T.zg = src.zmask & ~tile;
+        }
+        T.k0 = pc64(src.xmask & src.zmask) & 3;
+        T.chunk = 0;
+        if (G.mode == XG_DIAG && src.zmask) {
+          const int lo = __builtin_ctzll(src.zmask), hi = 63 - __builtin_clzll(src.zmask);
+          if (lo / EXP_CHUNK_BITS == hi / EXP_CHUNK_BITS) T.chunk = 1 + lo / EXP_CHUNK_BITS;
+        }
+        if (T.chunk) D.direct = (int16_t)X->nterms;
+        (T.k0 & 1 ? odd : even)++;
+      }
+      D.part = (int8_t)(G.mode == XG_DIAG ? 0 : odd == 0 ? 1 : even == 0 ? 2 : 0);
+      D.coef = (int16_t)X->ncoef;
+      // Re(i^kk v) = vr, -vi, -vr, vi for kk = 0..3: coefficient of vr and of vi
+      auto add = [](double2& C, int kk, double c2) {
+        switch (kk & 3) {
+          case 0: C.x += c2; break;
+          case 1: C.y -= c2; break;
+          case 2: C.x -= c2; break;
+          default: C.y += c2; break;
+        }
+      };
+      if (G.mode == XG_CLASS) {
+        // class c: the lower x bits of i are deposit(c); j = i ^ x
+        const int W = pc64(G.x) - 1;
+        const uint64_t xlo = G.x & ~(1ull << (63 - __builtin_clzll(G.x)));
+        for (int c = 0; c < (1 << W); c++) {
+          uint64_t dep = 0, mk = xlo;
+          for (int b = 0; mk; b++) {
+            const int bit = __builtin_ctzll(mk);
+            mk &= mk - 1;
+            if (c >> b & 1) dep |= 1ull << bit;
+          }
+          const uint64_t jx = dep ^ G.x;
+          double2 C = make_double2(0.0, 0.0);
+          for (int q = D.first; q < D.first + D.count; q++) {
+            const lq_pauli_term& src = terms[order[q - D.first]];
+            add(C, X->terms[q].k0 + 2 * (pc64(jx & src.zmask) & 1), X->terms[q].c);
+          }
+          X->coef[X->ncoef++] = C;
+        }
+      } else if (G.mode == XG_TABLE) {
+        // index bit t = parity(j & z_t)
+        for (int idx = 0; idx < (1 << D.count); idx++) {
+          double2 C = make_double2(0.0, 0.0);
+          for (int q = 0; q < D.count; q++)
+            add(C, X->terms[D.first + q].k0 + 2 * (idx >> q & 1), X->terms[D.first + q].c);
+          X->coef[X->ncoef++] = C;
+        }
+      }
+      if (G.mode == XG_DIAG) {
+        X->diag = X->ngroups - 1;
+        for (int q = D.first; q < D.first + D.count; q++)
+          if (X->terms[q].chunk) X->tables = 1;
+      }
+    }
+    Q.g1 = X->ngroups;
+  }
+  return (int)out.size();
+}
+
+// ---------------------------------------------------------------- kernel
+
+// Class-mode sums over this thread's indices j of the tile (j runs over the
+// k - w bits outside x): amplitude i = expand(j) | dep[c] (lower x bits = class
+// c, top x bit clear) pairs with i ^ x; sr[c] += Re conj(psi_i) psi_{i^x},
+// si[c] += Im (as `part` asks).  Every class of an index is handled by the same
+// thread, so the index expansion is shared.
+template <int BLOCK, int W>
+__device__ __forceinline__ void xp_class_sums(const double2* __restrict__ sm, uint32_t T,
+                                              uint32_t x, int part, const uint32_t* dep,
+                                              double* sr, double* si) {
+  constexpr int NC = 1 << W;
+  const uint32_t cnt = T >> (W + 1);
+  // the x bit positions, ascending (zero bits are inserted lowest first)
+  int pos[W + 1];
+  {
+    uint32_t mk = x;
+#pragma unroll
+    for (int b = 0; b <= W; b++) {
+      pos[b] = __ffs(mk) - 1;
+      mk &= mk - 1;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; c++) sr[c] = si[c] = 0.0;
+  constexpr int NL = NC < 2 ? NC : 2;   // classes loaded together (register budget)
+  for (uint32_t j = threadIdx.x; j < cnt; j += BLOCK) {
+    uint32_t a = j;
+#pragma unroll
+    for (int b = 0; b <= W; b++) a = insert0(a, pos[b]);
+#pragma unroll
+    for (int c0 = 0; c0 < NC; c0 += NL) {
+      double2 A[NL], B[NL];
+#pragma unroll
+      for (int c = 0; c < NL; c++) {
+        A[c] = sm[a | dep[c0 + c]];
+        B[c] = sm[(a | dep[c0 + c]) ^ x];
+      }
+#pragma unroll
+      for (int c = 0; c < NL; c++) {
+        if (part != 2) sr[c0 + c] = fma(A[c].y, B[c].y, fma(A[c].x, B[c].x, sr[c0 + c]));
+        if (part != 1) si[c0 + c] = fma(-A[c].y, B[c].x, fma(A[c].x, B[c].y, si[c0 + c]));
+      }
+    }
+  }
+}
+
+template <int BLOCK, int W>
+__device__ __forceinline__ double xp_class_group(const double2* __restrict__ sm, uint32_t T,
+                                                 const XGroup& G,
+                                                 const double2* __restrict__ coef) {
+  constexpr int NC = 1 << W;
+  uint32_t dep[NC];
+  // deposit the class bits into the lower x bits (ascending)
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    uint32_t d = 0, mk = G.x & ~(1u << G.h);
+    for (int b = 0; mk; b++) {
+      const int bit = __ffs(mk) - 1;
+      mk &= mk - 1;
+      if (c >> b & 1) d |= 1u << bit;
+    }
+    dep[c] = d;
+  }
+  double sr[NC], si[NC];
+  xp_class_sums<BLOCK, W>(sm, T, G.x, G.part, dep, sr, si);
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < NC; c++) {
+    const double2 C = coef[G.coef + c];
+    if (G.part != 2) acc = fma(C.x, sr[c], acc);
+    if (G.part != 1) acc = fma(C.y, si[c], acc);
+  }
+  return acc;
+}
+
+// One CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of every
+// pass of the plan (state blockIdx.y) and writes its partial sum.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_constant__ XPlan X,
+                                                               const double2* __restrict__ states,
+                                                               uint64_t stride,
+                                                               double* __restrict__ partial) {
+  // dynamic shared memory: the tile, then the coefficient table, then the
+  // diagonal chunk tables
+  extern __shared__ double2 xsm[];
+  __shared__ uint32_t hioff[1 << (XP_TILE_BITS - 5)];   // k - m <= XP_TILE_BITS - 5
+  __shared__ double red[BLOCK / 32];
+  const uint32_t tid = threadIdx.x;
+  const double2* __restrict__ st = states + blockIdx.y * stride;
+  const int n = X.n;
+  const int nch = (n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS;
+  const uint32_t Tmax = X.npass ? 1u << X.passes[0].k : 0u;
+  double2* coef = xsm + Tmax;
+  double* tab = reinterpret_cast<double*>(coef + X.ncoef);
+  for (int e = tid; e < X.ncoef; e += BLOCK) coef[e] = X.coef[e];
+  if (X.tables && X.diag >= 0) {
+    // tab[c][v] = sum of the chunk-c diagonal terms c_t (-1)^popcount(v & z_t)
+    const XGroup& G = X.groups[X.diag];
+    for (int e = tid; e < nch * 256; e += BLOCK) {
+      const int c = e >> 8, v = e & 255;
+      double s = 0.0;
+      for (int t = G.first; t < G.first + G.count; t++) {
+        if (X.terms[t].chunk != c + 1) continue;
+        const uint32_t zc = (uint32_t)(X.terms[t].zg >> (EXP_CHUNK_BITS * c)) & 255u;
+        s += (__popc((uint32_t)v & zc) & 1) ? -X.terms[t].c : X.terms[t].c;
+      }
+      tab[e] = s;
+    }
+  }
+  double acc = 0.0;
+  for (int p = 0; p < X.npass; p++) {
+    const XPass& Q = X.passes[p];
+    const int k = Q.k, m = Q.m, kh = k - m;
+    const uint32_t T = 1u << k, lowmask = (1u << m) - 1u;
+    __syncthreads();
+    for (uint32_t j = tid; j < (1u << kh); j += BLOCK)
+      hioff[j] = (uint32_t)(deposit(j, Q.tbits + m, kh) >> m);
+    __syncthreads();
+    const uint64_t ntiles = 1ull << (n - k);
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const uint64_t base = deposit(t, Q.obits, Q.nobits);
+      const double2* __restrict__ sm = xsm;
+      for (uint32_t s = tid; s < T; s += BLOCK)
+        xsm[s] = st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)];
+      __syncthreads();
+      for (int g = Q.g0; g < Q.g1; g++) {
+        const XGroup& G = X.groups[g];
+        if (G.mode == XG_CLASS) {
+          if (G.w == 1)
+            acc += xp_class_group<BLOCK, 0>(sm, T, G, coef);
+          else if (G.w == 2)
+            acc += xp_class_group<BLOCK, 1>(sm, T, G, coef);
+          else
+            acc += xp_class_group<BLOCK, 2>(sm, T, G, coef);
+        } else if (G.mode == XG_DIAG) {
+          for (uint32_t s = tid; s < T; s += BLOCK) {
+            const uint64_t gi = base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask);
+            const double2 v = sm[s];
+            const double pr = fma(v.x, v.x, v.y * v.y);
+            double d = 0.0;
+            if (X.tables)
+              for (int c = 0; c < nch; c++) d += tab[c * 256 + ((gi >> (EXP_CHUNK_BITS * c)) & 255)];
+            for (int q = X.tables ? G.direct : G.first; q < G.first + G.count; q++) {
+              const XTerm& Tm = X.terms[q];
+              const uint32_t f = (uint32_t)(__popcll(gi & Tm.zg) & 1) << 31;
+              d += xsign(Tm.c, f);
+            }
+            acc = fma(d, pr, acc);
+          }
+        } else {
+          // table mode: index bit q = parity(j & z_q), CTA part per tile
+          uint32_t gmask = 0, zl[XP_TABLE_TERMS];
+#pragma unroll
+          for (int q = 0; q < XP_TABLE_TERMS; q++) {
+            zl[q] = q < G.count ? X.terms[G.first + q].zl : 0u;
+            if (q < G.count) gmask |= (uint32_t)(__popcll(base & X.terms[G.first + q].zg) & 1) << q;
+          }
+          const uint32_t x = G.x;
+          const int h = G.h;
+          const double2* __restrict__ C = coef + G.coef;
+          const int part = G.part;
+          for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
+            const uint32_t i0 = insert0(j, h), j0 = i0 ^ x;
+            const double2 A = sm[i0], B = sm[j0];
+            uint32_t idx = gmask;
+#pragma unroll
+            for (int q = 0; q < XP_TABLE_TERMS; q++) idx ^= (uint32_t)(__popc(j0 & zl[q]) & 1) << q;
+            const double2 w = C[idx];
+            if (part != 2) acc = fma(w.x, fma(A.x, B.x, A.y * B.y), acc);
+            if (part != 1) acc = fma(w.y, fma(A.x, B.y, -(A.y * B.x)), acc);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0;
+    for (int w = 0; w < BLOCK / 32; w++) s += red[w];
+    partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+static constexpr int kXBlock = 256;
+
+cudaError_t launch_expval_tiled(const XPlan& X, const double2* states, uint64_t stride,
+                                int nstates, double* partial, double* out, int accumulate,
+                                cudaStream_t s) {
+  (void)cudaGetLastError();  // report only this launcher's own errors
+  const int k = X.npass ? X.passes[0].k : 0;
+  const int nch = (X.n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS;
+  const size_t smem = (sizeof(double2) << k) + sizeof(double2) * X.ncoef +
+                      (X.tables ? sizeof(double) * 256 * nch : 0);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(
+        expval_tile_kernel<kXBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)((sizeof(double2) << XP_TILE_BITS) + sizeof(double2) * XP_MAX_COEF +
+              sizeof(double) * 256 * ((34 + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS)));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  // one wave of resident CTAs (the launch bound allows 4 per SM; shared
+  // memory, with ~1.5 KiB static and 1 KiB reserved, may allow fewer)
+  int per_sm = (int)((228u << 10) / (smem + (3u << 10)));
+  per_sm = per_sm < 1 ? 1 : per_sm > 4 ? 4 : per_sm;
+  int gx = expval_grid(X.n);
+  if (gx > sm_count() * per_sm) gx = sm_count() * per_sm;
+  dim3 grid(gx, nstates);
+  expval_tile_kernel<kXBlock><<<grid, kXBlock, smem, s>>>(X, states, stride, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_sum_partials(partial, gx, nstates, out, accumulate, s);
+}
+
+}  // namespace lq

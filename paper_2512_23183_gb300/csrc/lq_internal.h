@@ -221,6 +221,10 @@ lq_status lower_circuit(int n, const lq_gate* gates, int ng, const double* param
 // tile kernels.
 double op_flops(const LOp& o, int n);
 
+// The autotuner's schedule options for this circuit structure on the current
+// GPU (lq_tune.cu); false (opt untouched) when it has not been tuned.
+bool tuned_options(int n, const lq_gate* gates, int ng, ScheduleOptions* opt);
+
 // Validation helpers.
 lq_status check_n(int n);
 lq_status check_gates(int n, const lq_gate* gates, int ng, const double* params, int np);

@@ -71,20 +71,6 @@ const double2* dyadic_tables(cudaError_t* err) {
 
 // ----------------------------------------------------------- tile passes
 
-// 16-byte asynchronous global -> shared copy (completion by
-// cp.async.wait_group, a hardware wait: no spin loop).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // One CTA processes tiles w = blockIdx.x, blockIdx.x + gridDim.x, ... of the
 // `nstates` states (stride `stride` amplitudes apart); a tile is the 2^k
 // amplitudes base | deposit(s, tbits), s < 2^k.  Tile loads and stores are
@@ -376,6 +362,13 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int npar
   double s = 0;
   for (int p = 0; p < nparts; p++) s += partial[(uint64_t)sidx * nparts + p];
   out[sidx] = accumulate ? out[sidx] + s : s;
+}
+
+cudaError_t launch_sum_partials(const double* partial, int nparts, int nstates, double* out,
+                                int accumulate, cudaStream_t s) {
+  sum_partials_kernel<<<(nstates + 127) / 128, 128, 0, s>>>(partial, nparts, nstates, out,
+                                                             accumulate);
+  return cudaGetLastError();
 }
 
 static constexpr int kExpBlock = 256;

@@ -40,6 +40,55 @@ struct ExpParams {
 };
 static_assert(sizeof(ExpParams) < 32000, "ExpParams exceeds the kernel parameter budget");
 
+// Tiled <H> (lq_expval.cu): terms grouped by X mask, groups packed into tile
+// passes whose tile bits cover their X masks.
+constexpr int XP_TILE_BITS = 12;   // largest tile (the plan picks 11 or 12)
+constexpr int kTiledExpvalMinN = 12;   // smaller states use the untiled kernel
+constexpr int XP_MAX_PASS = 48;
+constexpr int XP_MAX_GROUPS = 192;
+constexpr int XP_MAX_TERMS = 512;
+constexpr int XP_MAX_COEF = 384;
+constexpr int XP_TABLE_TERMS = 4;   // terms per table-mode group
+enum XGroupMode : int8_t { XG_DIAG = 0, XG_CLASS = 1, XG_TABLE = 2 };
+struct XTerm {
+  double c;        // c_t (diagonal) or 2 c_t (pair terms)
+  uint64_t zg;     // Z mask outside the tile (diagonal terms: the whole Z mask)
+  uint32_t zl;     // Z mask inside the tile (tile-local bits)
+  int16_t k0;      // number of Y factors mod 4
+  int16_t chunk;   // diagonal terms: 1 + the 8-bit index chunk holding z, or 0
+};
+struct XGroup {
+  uint32_t x;        // X mask (tile-local bits); 0 for the diagonal group
+  int16_t first, count;
+  int16_t coef;      // class mode: 2^{w-1} entries; table mode: 2^count entries
+  int8_t h, w;       // top bit of x, number of x bits
+  int8_t mode, part; // XGroupMode; part 1: only Re, 2: only Im, 0: both
+  int16_t direct;    // diagonal group: first term not read from a chunk table
+};
+struct XPass {
+  int32_t k, m, nobits, g0, g1, pad;
+  int8_t tbits[16];
+  int8_t obits[48];
+};
+struct XPlan {
+  int32_t n, npass, ngroups, nterms, ncoef, tables, diag, pad;
+  XPass passes[XP_MAX_PASS];
+  XGroup groups[XP_MAX_GROUPS];
+  XTerm terms[XP_MAX_TERMS];
+  double2 coef[XP_MAX_COEF];   // (coefficient of Re, coefficient of Im) per entry
+};
+static_assert(sizeof(XPlan) < 32000, "XPlan exceeds the kernel parameter budget");
+// Build the tile-pass plans (one or more launches) of a term list with 2^k
+// tiles; terms whose X mask does not fit a tile go to `wide`.  Returns the
+// number of plans, or -1 on an internal limit.
+int build_xplans(int n, const lq_pauli_term* terms, int nt, int k, std::vector<XPlan>& out,
+                 std::vector<lq_pauli_term>& wide);
+cudaError_t launch_expval_tiled(const XPlan& X, const double2* states, uint64_t stride,
+                                int nstates, double* partial, double* out, int accumulate,
+                                cudaStream_t s);
+cudaError_t launch_sum_partials(const double* partial, int nparts, int nstates, double* out,
+                                int accumulate, cudaStream_t s);
+
 // Group a term list by X mask into chunks that fit ExpParams.  Returns the
 // number of chunks written to `chunks` (caller-allocated with capacity
 // `max_chunks`), or -1 when max_chunks is too small.

@@ -328,6 +328,11 @@ static std::vector<int> fft_bounds(int n) {
   return bounds;
 }
 
+// Gates of Alg. 3 without its final swap network: for i, H(i) then CP(pi /
+// 2^{j-i}) with control i and target j > i (the inverse: reversed order,
+// conjugated phases).  The floor(n/2) SWAP(i, n-1-i) gates reverse the bits of
+// the index; they run as one bit-reversal pass (after the gates, or before
+// them for the inverse).
 static std::vector<lq_gate> qft_gate_list(int n, int inverse) {
   const double PI = 3.14159265358979323846;
   std::vector<lq_gate> g;
@@ -346,7 +351,6 @@ static std::vector<lq_gate> qft_gate_list(int n, int inverse) {
     g.push_back(mk(LQ_H, i, -1, 0));
     for (int j = i + 1; j < n; j++) g.push_back(mk(LQ_CP, i, j, PI / std::ldexp(1.0, j - i)));
   }
-  for (int i = 0; i < n / 2; i++) g.push_back(mk(LQ_SWAP, i, n - 1 - i, 0));
   if (inverse) {
     std::vector<lq_gate> r(g.rbegin(), g.rend());
     for (auto& G : r)
@@ -362,7 +366,13 @@ extern "C" lq_status lq_qft_plan(int n, int method, lq_plan_info* out) {
   if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
   if (method == LQ_QFT_GATES) {
     std::vector<lq_gate> g = qft_gate_list(n, 0);
-    return lq_circuit_plan(n, g.data(), (int)g.size(), nullptr, 0, out);
+    st = lq_circuit_plan(n, g.data(), (int)g.size(), nullptr, 0, out);
+    if (st) return st;
+    if (n > 1) {   // the bit-reversal pass
+      out->npasses += 1;
+      out->dram_bytes += 32.0 * std::ldexp(1.0, n);
+    }
+    return LQ_OK;
   }
   if (method != LQ_QFT_FFT) return fail(LQ_ERR_INVALID_ARG, "unknown QFT method %d", method);
   std::vector<int> b = fft_bounds(n);
@@ -398,9 +408,17 @@ extern "C" lq_status lq_qft(void* amps, int n, int inverse, int method, void* sc
   double2* psi = (double2*)amps;
   if (method == LQ_QFT_GATES) {
     // Alg. 3: for i: H(i), CP(pi/2^{j-i}) control i target j > i; then the
-    // swaps.  The inverse is the reversed sequence with conjugated phases.
+    // swaps (one bit-reversal pass).  The inverse is the reversed sequence
+    // with conjugated phases.
     std::vector<lq_gate> g = qft_gate_list(n, inverse);
-    return lq_apply_circuit(amps, n, g.data(), (int)g.size(), nullptr, 0, stream);
+    cudaError_t e = cudaSuccess;
+    if (inverse && n > 1 && (e = launch_bitrev(psi, n, s)) != cudaSuccess)
+      return fail(LQ_ERR_CUDA, "bit reversal: %s", cudaGetErrorString(e));
+    st = lq_apply_circuit(amps, n, g.data(), (int)g.size(), nullptr, 0, stream);
+    if (st) return st;
+    if (!inverse && n > 1 && (e = launch_bitrev(psi, n, s)) != cudaSuccess)
+      return fail(LQ_ERR_CUDA, "bit reversal: %s", cudaGetErrorString(e));
+    return LQ_OK;
   }
   cudaError_t e = fft_tables_init(s);
   if (e != cudaSuccess) return fail(LQ_ERR_CUDA, "fft tables: %s", cudaGetErrorString(e));

@@ -161,6 +161,61 @@ def test_expval_many_terms_chunked(lq):
     assert lq.expval_pauli_sum(dev(psi), n, []) == 0.0
 
 
+def _pauli(n, ops, c=1.0):
+    """(c, string) with ops = {qubit: 'X'|'Y'|'Z'}."""
+    s = ["I"] * n
+    for q, ch in ops.items():
+        s[q] = ch
+    return (float(c), "".join(s))
+
+
+@pytest.mark.parametrize("n,ring", [(12, False), (13, True), (16, True), (18, False)])
+def test_expval_tiled_heisenberg(lq, n, ring):
+    # XX + YY share an X mask with Z inside it (class mode); ZZ is diagonal
+    terms = W.heisenberg(n, ring=ring) + W.z_field(n, 0.3)
+    psi = W.gaussian_state(n, 40 + n)
+    assert close_e(lq.expval_pauli_sum(dev(psi), n, terms), oracle.expval(psi, n, terms))
+
+
+@pytest.mark.parametrize("n,seed", [(12, 1), (14, 2), (17, 3)])
+def test_expval_tiled_random(lq, n, seed):
+    # table mode: Z factors outside the X mask, every Y parity mix
+    rng = np.random.default_rng(100 + seed)
+    terms = W.random_pauli_sum(n, 80, rng, kmin=1, kmax=4)
+    psi = W.gaussian_state(n, 50 + seed)
+    assert close_e(lq.expval_pauli_sum(dev(psi), n, terms), oracle.expval(psi, n, terms))
+
+
+def test_expval_tiled_group_shapes(lq):
+    n = 15
+    rng = np.random.default_rng(7)
+    terms = []
+    # eleven terms on one X mask (split into table-mode groups of four)
+    for _ in range(11):
+        ops = {0: "X", 9: "Y"}
+        for q in rng.choice([2, 3, 5, 12, 14], size=2, replace=False):
+            ops[int(q)] = "Z"
+        terms.append(_pauli(n, ops, rng.normal()))
+    # class mode with an odd Y count (only Im) and with both parities (Re and Im)
+    terms.append(_pauli(n, {3: "X", 4: "Y"}, 0.7))
+    terms.append(_pauli(n, {3: "Y", 4: "X"}, -0.4))
+    terms.append(_pauli(n, {6: "X", 7: "X"}, 0.9))
+    terms.append(_pauli(n, {6: "X", 7: "Y"}, 0.5))
+    terms.append(_pauli(n, {1: "Y", 8: "Y", 13: "X"}, -1.1))   # three X bits, four classes
+    terms.append(_pauli(n, {11: "X"}, 0.25))                     # one X bit
+    terms.append(_pauli(n, {10: "Y"}, -0.35))
+    # X masks wider than a tile (the untiled kernel) and diagonal terms across chunks
+    terms.append((0.6, "X" * n))
+    terms.append((-0.2, "XY" * (n // 2) + "Z"))
+    terms.append(_pauli(n, {0: "Z", 14: "Z"}, 0.8))
+    terms.append(_pauli(n, {2: "Z", 5: "Z", 9: "Z"}, -0.45))
+    psi = W.gaussian_state(n, 77)
+    assert close_e(lq.expval_pauli_sum(dev(psi), n, terms), oracle.expval(psi, n, terms))
+    # diagonal only, and wide only
+    for sub in (terms[-2:] + W.z_field(n, 0.1), terms[-4:-2]):
+        assert close_e(lq.expval_pauli_sum(dev(psi), n, sub), oracle.expval(psi, n, sub))
+
+
 @pytest.mark.parametrize("n", [2, 7, 13])
 def test_apply_pauli_sum(lq, n):
     import torch

@@ -1,0 +1,73 @@
+"""The schedule autotuner on the GPU: the chosen schedule is at least as
+fast as the default on the same call, is used by apply_circuit and
+circuit_plan for every circuit of the same structure, gives results equal to
+the oracle's, and survives a save / clear / load of the cache."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ATOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def lq():
+    import paper_2512_23183_gb300 as m
+
+    m.load()
+    m.tune_cache_clear()
+    yield m
+    m.tune_cache_clear()
+
+
+def _dev(psi):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+
+
+@pytest.mark.parametrize("n,depth", [(14, 2), (18, 1)])
+def test_autotune_choice_and_parity(lq, n, depth, tmp_path):
+    gates, P = W.hea(n, depth, "ring")
+    r = lq.autotune(n, gates, W.angles(P, 3))
+    assert r["candidates"] >= 4
+    assert 9 <= r["tile_bits"] <= 12 and r["low_bits"] in (5, 6)
+    assert r["ms"] <= r["ms_default"]
+    assert lq.circuit_plan(n, gates, W.angles(P, 4))["tile_bits"] == r["tile_bits"]
+    # the tuned schedule serves other parameter values of the same structure
+    for seed in (4, 5):
+        th = W.angles(P, seed)
+        psi = W.gaussian_state(n, seed)
+        t = _dev(psi)
+        lq.apply_circuit(t, n, gates, th)
+        want = oracle.apply_circuit(psi.copy(), n, gates, th)
+        np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
+    # save, clear, load: the same choice comes back
+    f = tmp_path / "tune.txt"
+    lq.tune_cache_save(str(f))
+    lq.tune_cache_clear()
+    assert lq.tune_cache_size() == 0
+    lq.tune_cache_load(str(f))
+    assert lq.circuit_plan(n, gates, W.angles(P, 4))["tile_bits"] == r["tile_bits"]
+
+
+def test_autotune_qft_gate_circuit(lq):
+    # a circuit with merged dyadic and one-bit phases
+    n = 15
+    gates = []
+    for i in range(n):
+        gates.append(W.G("H", i))
+        for j in range(i + 1, min(n, i + 5)):
+            gates.append(W.G("CP", i, j, angle=np.pi / 2 ** (j - i)))
+        gates.append(W.G("RZ", i, param=i))
+    th = W.angles(n, 9)
+    r = lq.autotune(n, gates, th)
+    psi = W.gaussian_state(n, 12)
+    t = _dev(psi)
+    lq.apply_circuit(t, n, gates, th)
+    want = oracle.apply_circuit(psi.copy(), n, gates, th)
+    np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
+    assert r["ms"] <= r["ms_default"]

@@ -1,0 +1,66 @@
+"""The autotuner's cache file (host only, no GPU): entries load, save and
+merge; a malformed file is rejected and leaves the cache unchanged."""
+import os
+
+import pytest
+
+import paper_2512_23183_gb300 as lq
+
+GOOD = """# lq autotune cache v1: gpu n hash k m table ms ms_default
+NVIDIA_GB300|152 24 00000000deadbeef 11 5 1 3.250000 3.900000
+NVIDIA_GB300|152 30 0123456789abcdef 10 6 0 210.500000 222.000000
+"""
+
+
+@pytest.fixture()
+def L():
+    lib = lq.load()
+    lq.tune_cache_clear()
+    yield lib
+    lq.tune_cache_clear()
+
+
+def test_load_save_round_trip(L, tmp_path):
+    src = tmp_path / "tune.txt"
+    src.write_text(GOOD)
+    lq.tune_cache_load(str(src))
+    assert lq.tune_cache_size() == 2
+    out = tmp_path / "out.txt"
+    lq.tune_cache_save(str(out))
+    lines = [ln for ln in out.read_text().splitlines() if not ln.startswith("#")]
+    assert sorted(lines) == sorted(ln for ln in GOOD.splitlines() if not ln.startswith("#"))
+    # loading the same file again merges (no duplicates)
+    lq.tune_cache_load(str(out))
+    assert lq.tune_cache_size() == 2
+
+
+@pytest.mark.parametrize("bad", [
+    "NVIDIA_GB300|152 24 00000000deadbeef 11 5 1 3.25\n",          # missing field
+    "NVIDIA_GB300|152 40 00000000deadbeef 11 5 1 3.25 3.9\n",      # n out of range
+    "NVIDIA_GB300|152 24 deadbeef 11 5 1 3.25 3.9\n",              # short hash
+    "NVIDIA_GB300|152 24 00000000deadbeef 14 5 1 3.25 3.9\n",      # k too large
+    "NVIDIA_GB300|152 24 00000000deadbeef 9 10 1 3.25 3.9\n",      # m > k
+])
+def test_malformed_rejected(L, tmp_path, bad):
+    good = tmp_path / "good.txt"
+    good.write_text(GOOD)
+    lq.tune_cache_load(str(good))
+    f = tmp_path / "bad.txt"
+    f.write_text(GOOD + bad)
+    with pytest.raises(lq.LqError):
+        lq.tune_cache_load(str(f))
+    assert lq.tune_cache_size() == 2
+    with pytest.raises(lq.LqError):
+        lq.tune_cache_load(str(tmp_path / "missing.txt"))
+
+
+def test_plan_unaffected_by_other_gpus_entries(L, tmp_path):
+    import workloads as W
+
+    n = 16
+    gates, P = W.hea(n, 2, "ladder")
+    before = lq.circuit_plan(n, gates, W.angles(P, 1))
+    f = tmp_path / "t.txt"
+    f.write_text("Some_Other_GPU|1 16 %016x 12 6 0 1.0 2.0\n" % 0x1234)
+    lq.tune_cache_load(str(f))
+    assert lq.circuit_plan(n, gates, W.angles(P, 1)) == before
