@@ -645,6 +645,34 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
       out.op_src[p * MAX_OPS + cnt] = psrc[q];
       cnt++;
     }
+    if (opt.lphase_table) {
+      // table-mode dyadic ops: per-CTA partial-sum tables (256 words) and the
+      // CTA-decided factors (3 words each) in the pass's dyadic-table area
+      uint32_t words = 0;
+      for (int o = 0; o < cnt; o++) {
+        Op& d = P.ops[o];
+        if (d.type != OP_DPHASE) continue;
+        const double* F = P.coef + d.cidx;
+        bool ok = true;
+        int ncta = 0;
+        for (uint32_t f = 0; f < d.x_loc; f++) {
+          const uint64_t loc = dbits(F[4 * f]), gm = dbits(F[4 * f + 1]);
+          const uint32_t lm = (uint32_t)loc & ~d.cm_loc;
+          if (lm & (lm - 1)) ok = false;
+          if (lm && gm) ok = false;
+          if (!lm && gm) ncta++;
+        }
+        if (!ok || ncta > 255 || words + 256 + 3 * (uint32_t)ncta > DTAB_MAX_WORDS) continue;
+        d.mode |= DP_TABLE;
+        d.z_loc = words;
+        d.b1 = (uint8_t)ncta;
+        words += 256 + 3 * (uint32_t)ncta;
+      }
+      if (words) {
+        P.h.flags |= PF_DTAB;
+        P.h.dtab_words = (int32_t)words;
+      }
+    }
     if (p + 1 == passes.size() && need_scale) {
       LOp s;
       s.type = OP_SCALE;

@@ -293,15 +293,75 @@ __device__ __forceinline__ void diag_apply(double2* __restrict__ sm, uint32_t cn
   }
 }
 
+// Per-CTA tables of a table-mode OP_DPHASE at `out`: words 0..255 the two
+// 128-entry partial sums of the tile-bit weights (entry 0 of the first also
+// holds the weights that hold on every tile), then (CTA mask, CTA value,
+// weight) of each factor decided by CTA bits alone.  A factor that needs
+// s_b = 0 adds w to the constant and -w to c_b.  All threads call it; it
+// ends with a barrier.
+template <int BLOCK>
+__device__ __forceinline__ void build_dphase_table(unsigned long long* out, int k, const Op& op,
+                                                   const double* __restrict__ coef) {
+  __shared__ unsigned long long dt_c[MAX_TILE_BITS + 1];
+  const uint32_t tid = threadIdx.x;
+  const int nf = (int)op.x_loc;
+  const double* F = coef + op.cidx;
+  const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull;
+  if (tid <= (uint32_t)k) {
+    unsigned long long acc = 0;
+    for (int f = 0; f < nf; f++) {
+      const uint64_t loc = (uint64_t)__double_as_longlong(F[4 * f]);
+      const uint64_t gm = (uint64_t)__double_as_longlong(F[4 * f + 1]);
+      const unsigned long long w = (unsigned long long)__double_as_longlong(F[4 * f + 3]);
+      const uint32_t lm = (uint32_t)loc & ~op.cm_loc, lv = (uint32_t)(loc >> 32);
+      if (lm == 0) {
+        if (gm == 0 && tid == (uint32_t)k) acc += w;
+        continue;
+      }
+      const uint32_t b = (uint32_t)(__ffs(lm) - 1);
+      if (lv & lm) {
+        if (tid == b) acc += w;
+      } else {
+        if (tid == (uint32_t)k) acc += w;
+        if (tid == b) acc += (1ull << DYADIC_BITS) - w;
+      }
+    }
+    dt_c[tid] = acc & M34;
+  }
+  __syncthreads();
+  for (uint32_t v = tid; v < 256; v += BLOCK) {
+    const int c = v >> 7;
+    unsigned long long e = c ? 0ull : dt_c[k];
+    for (int b = 0; b < 7; b++)
+      if (((v & 127) >> b) & 1 && 7 * c + b < k) e += dt_c[7 * c + b];
+    out[v] = e & M34;
+  }
+  if (tid == 0) {
+    int q = 0;
+    for (int f = 0; f < nf; f++) {
+      const uint64_t loc = (uint64_t)__double_as_longlong(F[4 * f]);
+      const uint64_t gm = (uint64_t)__double_as_longlong(F[4 * f + 1]);
+      if (((uint32_t)loc & ~op.cm_loc) != 0 || gm == 0) continue;
+      out[256 + 3 * q] = gm;
+      out[256 + 3 * q + 1] = (uint64_t)__double_as_longlong(F[4 * f + 2]);
+      out[256 + 3 * q + 2] = (unsigned long long)__double_as_longlong(F[4 * f + 3]);
+      q++;
+    }
+  }
+  __syncthreads();
+}
+
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
 // are `base`; dtab: dyadic phase tables (hi: 2^17 entries exp(2 pi i h / 2^17),
 // lo: 2^17 entries exp(2 pi i l / 2^34)); ltab: the pass's per-CTA phase
-// table (table-mode OP_LPHASE), or nullptr.
+// table (table-mode OP_LPHASE), or nullptr; dpt: the pass's per-CTA dyadic
+// tables (table-mode OP_DPHASE), or nullptr.
 template <int BLOCK>
 __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, const Op& op,
                                          const double* __restrict__ coef, uint64_t base,
                                          const double2* __restrict__ dtab,
-                                         const double2* __restrict__ ltab = nullptr) {
+                                         const double2* __restrict__ ltab = nullptr,
+                                         const unsigned long long* __restrict__ dpt = nullptr) {
   const uint32_t tid = threadIdx.x;
   // per-tile tables of OP_DPHASE (2 x 128 sums) or OP_LPHASE (2 x 128
   // phases); one op at a time uses it
@@ -510,6 +570,27 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       const double* F = coef + op.cidx;
       const uint32_t cnt = T >> __popc(cm);
       const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull, LOMASK = (1ull << DYADIC_HALF) - 1ull;
+      if ((op.mode & DP_TABLE) && dpt) {
+        // per-CTA partial sums; the per-tile constant summed by each warp
+        const unsigned long long* tb = dpt + op.z_loc;
+        unsigned long long e0 = 0;
+        for (int q = (int)(tid & 31); q < (int)op.b1; q += 32)
+          if ((base & tb[256 + 3 * q]) == tb[256 + 3 * q + 1]) e0 += tb[256 + 3 * q + 2];
+        for (int o = 16; o > 0; o >>= 1) e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+        for (uint32_t j = tid; j < cnt; j += BLOCK) {
+          const uint32_t s = expand(j, cm, cv);
+          const unsigned long long e = (e0 + tb[s & 127] + tb[128 + ((s >> 7) & 127)]) & M34;
+          if (e == 0) continue;
+          double2 w = dtab[e >> DYADIC_HALF];
+          const unsigned long long lo = e & LOMASK;
+          if (lo) {
+            const double2 wl = dtab[(1u << DYADIC_HALF) + lo];
+            w = cmul(w, wl.x, wl.y);
+          }
+          sm[s] = cmul(sm[s], w.x, w.y);
+        }
+        break;
+      }
       if (tid <= MAX_TILE_BITS) dp_c[tid] = 0;
       if (tid == 0) {
         dp_e0 = 0;

@@ -103,7 +103,7 @@ struct PassHeader {
   int32_t nobits;
   int32_t flags;          // PF_* below
   int32_t ltab_op;        // PF_LTAB: index of the table-mode OP_LPHASE
-  int32_t reserved;
+  int32_t dtab_words;     // PF_DTAB: 64-bit words of the per-CTA dyadic tables
   uint64_t ntiles;        // 2^(n-k)
   const void* dtab;       // dyadic phase tables (device), set at launch
   int8_t tbits[16];       // tile-local bit j -> global bit position
@@ -115,7 +115,18 @@ enum PassFlags : int32_t {
   PF_DYADIC = 4,          // the pass has OP_DPHASE ops (needs dtab)
   PF_LTAB = 8,            // ops[ltab_op] is a table-mode OP_LPHASE: its 2^k-entry
                           // phase table is built once per CTA (pass_kernel only)
+  PF_DTAB = 16,           // some OP_DPHASE ops are in table mode (pass_kernel only)
 };
+
+// OP_DPHASE in table mode (Op::mode bit): every factor has at most one tile
+// bit beyond the op's common condition, and a factor with a tile bit has no
+// CTA-bit condition.  Then E(s) = e0(tile) + t0[s & 127] + t1[s >> 7] where
+// the two 128-entry partial-sum tables are the same for every tile: they are
+// built once per CTA (at word offset z_loc of the pass's dyadic-table area),
+// followed by the (CTA mask, CTA value, weight) triples of the b1 factors
+// decided by CTA bits alone, which each warp sums per tile with shuffles.
+constexpr uint8_t DP_TABLE = 0x80;
+constexpr uint32_t DTAB_MAX_WORDS = 4096;   // per pass (32 KiB of shared memory)
 
 // OP_LPHASE in table mode (Op::mode bit): every factor's condition bit is a
 // tile bit, so phase(s) is the same for every tile and one 2^k-entry table,
@@ -171,7 +182,8 @@ struct ScheduleOptions {
   int m = 5;                 // contiguous low bits always in the tile
   bool force_scale = false;  // always end with a (final) OP_SCALE
   bool merge_params = true;  // merge one-bit phases of parametrised gates too
-  bool lphase_table = false; // mark one OP_LPHASE per pass for a per-CTA table
+  bool lphase_table = false; // mark one OP_LPHASE per pass for a per-CTA table,
+                             // and OP_DPHASE ops for per-CTA partial-sum tables
                              // (schedules run by pass_kernel only)
 };
 

@@ -98,6 +98,15 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
     build_lphase_table<BLOCK>(t, k, P.ops[P.h.ltab_op], P.coef);
     ltab = t;
   }
+  const unsigned long long* dpt = nullptr;
+  if (P.h.flags & PF_DTAB) {
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(
+        smem_tiles + (dbuf ? 2 * T : T) + ((P.h.flags & PF_LTAB) ? T : 0));
+    for (int o = 0; o < nops; o++)
+      if (P.ops[o].type == OP_DPHASE && (P.ops[o].mode & DP_TABLE))
+        build_dphase_table<BLOCK>(d + P.ops[o].z_loc, k, P.ops[o], P.coef);
+    dpt = d;
+  }
   const uint64_t ntiles = P.h.ntiles;
   const uint64_t total = ntiles * (uint64_t)nstates;
   const bool zero = (P.h.flags & PF_INIT_ZERO) != 0;
@@ -137,7 +146,7 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
     }
     __syncthreads();
     for (int o = 0; o < nops; o++) {
-      apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab, ltab);
+      apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab, ltab, dpt);
       __syncthreads();
     }
     if (store) {
@@ -158,11 +167,12 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
   const size_t tile = sizeof(double2) << P.h.k;
   // double buffering for passes that load from HBM with tiles of <= 2^11
   const int dbuf = (P.h.k <= 11 && !(P.h.flags & PF_INIT_ZERO)) ? 1 : 0;
-  const size_t smem = tile * ((dbuf ? 2 : 1) + ((P.h.flags & PF_LTAB) ? 1 : 0));
+  const size_t smem = tile * ((dbuf ? 2 : 1) + ((P.h.flags & PF_LTAB) ? 1 : 0)) +
+                      ((P.h.flags & PF_DTAB) ? sizeof(unsigned long long) * P.h.dtab_words : 0);
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(pass_kernel<kPassBlock>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double2) << MAX_TILE_BITS));
+                                         (int)(200u << 10));
     if (e != cudaSuccess) return e;
     configured = true;
   }
