@@ -429,6 +429,8 @@ def vqe_extras(device):
         "vqe_n16_d8_ring_256p": W.vqe_ring(16, 8, 3) + (16, 1, 3),
     }.items():
         r = {}
+        if n > 12:   # tile width of the batched launch (set-up, untimed)
+            r["autotune_batched"] = lq.autotune_param_shift(n, gates, th, terms, device=device)
         for meth, reps in ((lq.PSR_PLAIN, reps_p), (lq.PSR_BATCHED, reps_b)):
             ws = torch.empty(lq.load().lq_param_shift_workspace_size(n, len(th), len(terms), meth),
                              dtype=torch.uint8, device=device)

@@ -326,6 +326,19 @@ size_t lq_batch_workspace_size(const lq_problem* problems, int count);
 lq_status lq_batch_param_shift(const lq_problem* problems, int count, void* workspace,
                                size_t ws_bytes, lq_stream stream);
 
+/* Tile width of the persistent batched launch (lq_batch_param_shift and the
+ * batched lq_param_shift_grad) for states larger than 2^12 amplitudes, timed
+ * over 9..12 on the caller's workspace (sized by lq_batch_workspace_size /
+ * lq_param_shift_workspace_size, which cover every width) and recorded per
+ * batch structure (every problem's n, gate structure, circuit and term
+ * counts).  A batch whose states all fit shared memory has nothing to tune:
+ * candidates = 1.  Gradients computed while tuning are discarded. */
+lq_status lq_autotune_batch(const lq_problem* problems, int count, void* workspace,
+                            size_t ws_bytes, lq_tune_result* out, lq_stream stream);
+lq_status lq_autotune_param_shift(int n, const lq_gate* gates, int ng, const double* params,
+                                  int np, const lq_pauli_term* terms, int nt, void* workspace,
+                                  size_t ws_bytes, lq_tune_result* out, lq_stream stream);
+
 /* ---------------------------------------------------------------------------
  * VQE outer loop (Sec. VI-B): Adam on E(theta), each gradient on the GPU.
  * The paper's settings are lr = 1e-2, at most 350 iterations, tolerance 1e-7

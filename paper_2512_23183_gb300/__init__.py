@@ -99,6 +99,7 @@ EXPORTS = [
     "lq_server_submit", "lq_server_wait", "lq_server_destroy", "lq_vqe_workspace_size",
     "lq_vqe_adam", "lq_adjoint_plan", "lq_expval_plan", "lq_autotune_circuit",
     "lq_tune_cache_save", "lq_tune_cache_load", "lq_tune_cache_clear", "lq_tune_cache_size",
+    "lq_autotune_batch", "lq_autotune_param_shift",
 ]
 
 
@@ -169,6 +170,11 @@ def load(build_if_missing=True):
     L.lq_expval_plan.argtypes = [ctypes.c_int, P(LqPauliTerm), ctypes.c_int, P(LqPlanInfo)]
     L.lq_autotune_circuit.argtypes = [c_void_p, ctypes.c_int, P(LqGate), ctypes.c_int,
                                       P(c_double), ctypes.c_int, P(LqTuneResult), c_void_p]
+    L.lq_autotune_batch.argtypes = [P(LqProblem), ctypes.c_int, c_void_p, c_size_t,
+                                    P(LqTuneResult), c_void_p]
+    L.lq_autotune_param_shift.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double),
+                                          ctypes.c_int, P(LqPauliTerm), ctypes.c_int, c_void_p,
+                                          c_size_t, P(LqTuneResult), c_void_p]
     L.lq_tune_cache_save.argtypes = [ctypes.c_char_p]
     L.lq_tune_cache_load.argtypes = [ctypes.c_char_p]
     L.lq_tune_cache_clear.argtypes = []
@@ -398,6 +404,39 @@ def autotune(n, gates, params=None, scratch=None, stream=None):
                 candidates=r.candidates, ms=r.ms, ms_default=r.ms_default)
 
 
+def _tune_dict(r):
+    return dict(tile_bits=r.tile_bits, low_bits=r.low_bits, phase_table=r.phase_table,
+                candidates=r.candidates, ms=r.ms, ms_default=r.ms_default)
+
+
+def autotune_batch(problems, device="cuda", stream=None, workspace=None):
+    """Pick the tile width of the persistent batched launch for this batch
+    structure (states larger than shared memory); returns the choice."""
+    L = load()
+    arr, keep = _problem_array(problems)
+    need = L.lq_batch_workspace_size(arr, len(problems))
+    ws = workspace if workspace is not None else _workspace(need, device)
+    r = LqTuneResult()
+    _check(L.lq_autotune_batch(arr, len(problems), _ptr(ws), ws.numel(), ctypes.byref(r),
+                               _stream(stream)))
+    return _tune_dict(r)
+
+
+def autotune_param_shift(n, gates, params, terms, device="cuda", stream=None, workspace=None):
+    """Pick the tile width of the batched parameter-shift launch of this
+    circuit structure; returns the choice."""
+    L = load()
+    g = pack_gates(gates)
+    t = pack_terms(terms, n)
+    p, pp, np_ = _params(params)
+    need = L.lq_param_shift_workspace_size(n, np_, len(terms), PSR_BATCHED)
+    ws = workspace if workspace is not None else _workspace(need, device)
+    r = LqTuneResult()
+    _check(L.lq_autotune_param_shift(n, g, len(gates), pp, np_, t, len(terms), _ptr(ws),
+                                     ws.numel(), ctypes.byref(r), _stream(stream)))
+    return _tune_dict(r)
+
+
 def tune_cache_save(path):
     _check(load().lq_tune_cache_save(os.fsencode(path)))
 
@@ -440,10 +479,7 @@ class BatchProblem:
         self.grad = None
 
 
-def batch_param_shift(problems, device="cuda", stream=None, workspace=None):
-    """Run many (n, circuit, H) problems' parameter-shift circuits in one
-    batched launch; fills problem.energy / problem.grad."""
-    L = load()
+def _problem_array(problems):
     arr = (LqProblem * len(problems))()
     keep = []
     for i, pb in enumerate(problems):
@@ -460,6 +496,14 @@ def batch_param_shift(problems, device="cuda", stream=None, workspace=None):
         P.terms = t
         P.energy = e.ctypes.data_as(ctypes.POINTER(c_double))
         P.grad = gr.ctypes.data_as(ctypes.POINTER(c_double))
+    return arr, keep
+
+
+def batch_param_shift(problems, device="cuda", stream=None, workspace=None):
+    """Run many (n, circuit, H) problems' parameter-shift circuits in one
+    batched launch; fills problem.energy / problem.grad."""
+    L = load()
+    arr, keep = _problem_array(problems)
     need = L.lq_batch_workspace_size(arr, len(problems))
     ws = workspace if workspace is not None else _workspace(need, device)
     _check(L.lq_batch_param_shift(arr, len(problems), _ptr(ws), ws.numel(), _stream(stream)))

@@ -17,6 +17,8 @@
 // its shifted gate and in the deferred scalar (a Patch).
 #include <cuda_runtime.h>
 
+#include <chrono>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -332,7 +334,8 @@ struct BatchPlan {
   std::size_t program_bytes = 0;
 };
 
-static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B) {
+static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B,
+                            int tile_bits = BATCH_TILE_BITS) {
   std::vector<double> cost;
   for (std::size_t pi = 0; pi < hps.size(); pi++) {
     const HostProblem& hp = hps[pi];
@@ -343,7 +346,7 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B) {
     lq_status st = lower_circuit(n, hp.gates, hp.ng, hp.params, hp.np, &ops, &nops, &zr, &zi);
     if (st) return st;
     ScheduleOptions opt;
-    opt.k = n <= BATCH_SMEM_BITS ? n : BATCH_TILE_BITS;
+    opt.k = n <= BATCH_SMEM_BITS ? n : tile_bits;
     opt.force_scale = true;
     opt.merge_params = false;   // shifted circuits patch individual gates
     Schedule S;
@@ -626,20 +629,88 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
   return LQ_OK;
 }
 
+// The tile widths the autotuner may pick for states larger than shared
+// memory; the workspace size covers every one of them.
+static const int kBatchTileChoices[] = {9, 10, 11, 12};
+
+static bool batch_has_tiles(const std::vector<HostProblem>& hps) {
+  for (const HostProblem& hp : hps)
+    if (hp.n > BATCH_SMEM_BITS) return true;
+  return false;
+}
+
+// Structure of a batch for the autotuner's cache: per problem n, the gate
+// structure, the number of circuits and of terms.
+static uint64_t batch_structure(const std::vector<HostProblem>& hps) {
+  uint64_t h = 0x6c71626174636821ull;
+  for (const HostProblem& hp : hps) {
+    const uint64_t rec[3] = {circuit_structure_hash(hp.n, hp.gates, hp.ng),
+                             (uint64_t)hp.patches.size(), (uint64_t)hp.nt};
+    for (uint64_t r : rec) h = (h ^ r) * 1099511628211ull + (h >> 29);
+  }
+  return h;
+}
+
 std::size_t batch_workspace_for(const std::vector<HostProblem>& hps, lq_status* st_out) {
-  BatchPlan B;
-  lq_status st = plan_batch(hps, B);
-  if (st_out) *st_out = st;
-  if (st) return 0;
-  return batch_bytes(B, batch_grid(B));
+  std::size_t need = 0;
+  for (int k : kBatchTileChoices) {
+    BatchPlan B;
+    lq_status st = plan_batch(hps, B, k);
+    if (st_out) *st_out = st;
+    if (st) return 0;
+    need = std::max(need, batch_bytes(B, batch_grid(B)));
+    if (!batch_has_tiles(hps)) break;   // the tile width does not matter
+  }
+  return need;
 }
 
 lq_status batch_run(const std::vector<HostProblem>& hps, void* ws, std::size_t ws_bytes,
                     cudaStream_t s, std::vector<double>& out) {
   BatchPlan B;
-  lq_status st = plan_batch(hps, B);
+  int k = BATCH_TILE_BITS;
+  if (batch_has_tiles(hps)) tuned_batch_tile(batch_structure(hps), &k);
+  lq_status st = plan_batch(hps, B, k);
   if (st) return st;
   return run_batch(B, ws, ws_bytes, s, out);
+}
+
+// Time the persistent batched launch for every tile width (host wall clock
+// around the graph-replayed run, which synchronises) and record the fastest.
+lq_status batch_autotune(const std::vector<HostProblem>& hps, void* ws, std::size_t ws_bytes,
+                         cudaStream_t s, lq_tune_result* res) {
+  double best = 1e300, def_ms = -1;
+  int bestk = BATCH_TILE_BITS, cands = 0;
+  const bool tiles = batch_has_tiles(hps);
+  for (int k : kBatchTileChoices) {
+    if (!tiles && k != BATCH_TILE_BITS) continue;
+    BatchPlan B;
+    lq_status st = plan_batch(hps, B, k);
+    if (st) return st;
+    std::vector<double> out;
+    double ms = 1e300;
+    for (int rep = 0; rep < 3; rep++) {
+      const auto t0 = std::chrono::steady_clock::now();
+      st = run_batch(B, ws, ws_bytes, s, out);
+      if (st) return st;
+      const double t = std::chrono::duration<double, std::milli>(
+                           std::chrono::steady_clock::now() - t0).count();
+      if (rep > 0 && t < ms) ms = t;   // the first run captures the graph
+    }
+    cands++;
+    if (k == BATCH_TILE_BITS) def_ms = ms;
+    if (ms < best) {
+      best = ms;
+      bestk = k;
+    }
+  }
+  if (tiles) record_batch_tile(batch_structure(hps), bestk, best, def_ms);
+  res->tile_bits = bestk;
+  res->low_bits = 5;
+  res->phase_table = 0;
+  res->candidates = cands;
+  res->ms = best;
+  res->ms_default = def_ms;
+  return LQ_OK;
 }
 
 }  // namespace lq
@@ -658,6 +729,19 @@ size_t lq_batch_workspace_size(const lq_problem* problems, int count) {
       return 0;
   }
   return batch_workspace_for(hps, nullptr);
+}
+
+lq_status lq_autotune_batch(const lq_problem* problems, int count, void* workspace,
+                            size_t ws_bytes, lq_tune_result* out, lq_stream stream) {
+  if (!problems || count <= 0 || !out) return fail(LQ_ERR_INVALID_ARG, "no problems");
+  std::vector<HostProblem> hps((std::size_t)count);
+  for (int i = 0; i < count; i++) {
+    const lq_problem& q = problems[i];
+    lq_status st = make_problem(q.n, q.gates, q.ng, q.params, q.np, q.terms, q.nt,
+                                q.want_grad != 0, false, hps[i]);
+    if (st) return st;
+  }
+  return batch_autotune(hps, workspace, ws_bytes, (cudaStream_t)stream, out);
 }
 
 lq_status lq_batch_param_shift(const lq_problem* problems, int count, void* workspace,

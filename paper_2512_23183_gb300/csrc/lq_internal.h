@@ -236,6 +236,11 @@ double op_flops(const LOp& o, int n);
 // The autotuner's schedule options for this circuit structure on the current
 // GPU (lq_tune.cu); false (opt untouched) when it has not been tuned.
 bool tuned_options(int n, const lq_gate* gates, int ng, ScheduleOptions* opt);
+// Structure hash of a circuit (n; per gate kind, qubits, whether it takes a
+// parameter, fixed angle / matrix) and the autotuner's batch entries.
+uint64_t circuit_structure_hash(int n, const lq_gate* gates, int ng);
+bool tuned_batch_tile(uint64_t structure, int* k);
+void record_batch_tile(uint64_t structure, int k, double ms, double ms_default);
 
 // Validation helpers.
 lq_status check_n(int n);

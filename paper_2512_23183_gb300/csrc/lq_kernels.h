@@ -124,6 +124,10 @@ std::size_t batch_workspace_for(const std::vector<HostProblem>& hps, lq_status* 
 // per problem E then its np gradient entries.
 lq_status batch_run(const std::vector<HostProblem>& hps, void* ws, std::size_t ws_bytes,
                     cudaStream_t s, std::vector<double>& out);
+// Times the batch for every tile width of its larger-than-shared-memory
+// states and records the fastest for this batch structure.
+lq_status batch_autotune(const std::vector<HostProblem>& hps, void* ws, std::size_t ws_bytes,
+                         cudaStream_t s, lq_tune_result* res);
 
 // --------------------------------------------------------------- launchers
 

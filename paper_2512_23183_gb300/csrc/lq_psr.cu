@@ -177,6 +177,29 @@ lq_status lq_param_shift_grad(int n, const lq_gate* gates, int ng, const double*
   return LQ_OK;
 }
 
+lq_status lq_autotune_param_shift(int n, const lq_gate* gates, int ng, const double* params,
+                                  int np, const lq_pauli_term* terms, int nt, void* workspace,
+                                  size_t ws_bytes, lq_tune_result* out, lq_stream stream) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  st = check_gates(n, gates, ng, params, np);
+  if (st) return st;
+  st = check_terms(n, terms, nt);
+  if (st) return st;
+  if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
+  std::vector<int> pg;
+  st = psr_param_gates(gates, ng, np, pg);
+  if (st) return st;
+  std::size_t need = lq_param_shift_workspace_size(n, np, nt, LQ_PSR_BATCHED);
+  if (!workspace || ws_bytes < need)
+    return fail(LQ_ERR_OOM, "workspace too small: %zu < %zu", ws_bytes, need);
+  HostProblem hp;
+  st = make_problem(n, gates, ng, params, np, terms, nt, true, false, hp);
+  if (st) return st;
+  std::vector<HostProblem> v(1, hp);
+  return batch_autotune(v, workspace, ws_bytes, (cudaStream_t)stream, out);
+}
+
 // ------------------------------------------------------------- Trotter
 
 lq_status lq_trotter_evolve(void* amps, int n, const lq_pauli_term* terms, int nt,

@@ -2,8 +2,10 @@
 // times the tile-pass schedules of lq_apply_circuit over tile width k,
 // contiguous low bits m and the per-CTA phase-table option, and keeps the
 // fastest in a process-wide cache that lq_apply_circuit (and lq_circuit_plan)
-// consult.  The cache can be written to and read from a text file, one line
-// per entry:
+// consult.  It also keeps, per batch structure, the tile width of the
+// persistent batched launch for states larger than shared memory
+// (lq_autotune_batch, n = 0 in the key).  The cache can be written to and
+// read from a text file, one line per entry:
 //   <gpu> <n> <structure hash, 16 hex digits> <k> <m> <table> <ms> <ms_default>
 // The structure hash covers n and, per gate, its kind, qubits, whether it
 // takes a parameter and (for fixed gates) its angle: everything the schedule
@@ -46,7 +48,9 @@ uint64_t fnv(uint64_t h, const void* p, std::size_t n) {
   return h;
 }
 
-uint64_t structure_hash(int n, const lq_gate* gates, int ng) {
+}  // namespace
+
+uint64_t circuit_structure_hash(int n, const lq_gate* gates, int ng) {
   uint64_t h = 1469598103934665603ull;
   h = fnv(h, &n, sizeof n);
   for (int i = 0; i < ng; i++) {
@@ -58,6 +62,8 @@ uint64_t structure_hash(int n, const lq_gate* gates, int ng) {
   }
   return h;
 }
+
+namespace {
 
 // "<device name>|<SM count>" with blanks replaced, for the current device.
 std::string gpu_id() {
@@ -77,11 +83,7 @@ std::string key_of(const std::string& gpu, int n, uint64_t h) {
   return gpu + buf;
 }
 
-}  // namespace
-
-bool tuned_options(int n, const lq_gate* gates, int ng, ScheduleOptions* opt) {
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  if (tune_cache().empty()) return false;
+const std::string& current_gpu() {
   static thread_local std::string gpu;
   static thread_local int gpu_dev = -1;
   int dev = 0;
@@ -90,7 +92,31 @@ bool tuned_options(int n, const lq_gate* gates, int ng, ScheduleOptions* opt) {
     gpu = gpu_id();
     gpu_dev = dev;
   }
-  auto it = tune_cache().find(key_of(gpu, n, structure_hash(n, gates, ng)));
+  return gpu;
+}
+
+}  // namespace
+
+// Batch entries use n = 0 in the key (the structure hash covers every
+// problem's n).
+bool tuned_batch_tile(uint64_t structure, int* k) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (tune_cache().empty()) return false;
+  auto it = tune_cache().find(key_of(current_gpu(), 0, structure));
+  if (it == tune_cache().end()) return false;
+  *k = it->second.k;
+  return true;
+}
+
+void record_batch_tile(uint64_t structure, int k, double ms, double ms_default) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_cache()[key_of(current_gpu(), 0, structure)] = TuneEntry{k, 5, 0, ms, ms_default};
+}
+
+bool tuned_options(int n, const lq_gate* gates, int ng, ScheduleOptions* opt) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (tune_cache().empty()) return false;
+  auto it = tune_cache().find(key_of(current_gpu(), n, circuit_structure_hash(n, gates, ng)));
   if (it == tune_cache().end()) return false;
   opt->k = it->second.k;
   opt->m = it->second.m;
@@ -179,7 +205,7 @@ lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng
   if (def_ms < 0) def_ms = best;   // small n: no k = 10 candidate
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    tune_cache()[key_of(gpu_id(), n, structure_hash(n, gates, ng))] =
+    tune_cache()[key_of(gpu_id(), n, circuit_structure_hash(n, gates, ng))] =
         TuneEntry{bestc.k, bestc.m, bestc.table, best, def_ms};
   }
   out->tile_bits = bestc.k;
@@ -222,7 +248,7 @@ lq_status lq_tune_cache_load(const char* path) {
     double ms, msd;
     if (std::sscanf(line, "%255s %d %31s %d %d %d %lf %lf", gpu, &n, hash, &k, &m, &table, &ms,
                     &msd) != 8 ||
-        n < 1 || n > 34 || k < 1 || k > MAX_TILE_BITS || m < 1 || m > k || std::strlen(hash) != 16) {
+        n < 0 || n > 34 || k < 1 || k > MAX_TILE_BITS || m < 1 || m > k || std::strlen(hash) != 16) {
       st = fail(LQ_ERR_INVALID_ARG, "%s:%d: malformed autotune entry", path, lineno);
       break;
     }

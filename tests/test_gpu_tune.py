@@ -71,3 +71,41 @@ def test_autotune_qft_gate_circuit(lq):
     want = oracle.apply_circuit(psi.copy(), n, gates, th)
     np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
     assert r["ms"] <= r["ms_default"]
+
+
+def test_autotune_param_shift_batch_tiles(lq):
+    # n = 14 > shared memory: the batched launch runs tiles of the tuned width
+    gates, th, terms = W.vqe_ring(14, 3, 2)
+    e0, g0 = lq.param_shift_grad(14, gates, th, terms, method=lq.PSR_BATCHED)
+    r = lq.autotune_param_shift(14, gates, th, terms)
+    assert r["candidates"] == 4 and 9 <= r["tile_bits"] <= 12
+    assert r["ms"] <= r["ms_default"]
+    e, g = lq.param_shift_grad(14, gates, th, terms, method=lq.PSR_BATCHED)
+    assert abs(e - e0) <= 1e-10 * max(1.0, abs(e0))
+    np.testing.assert_allclose(g, g0, rtol=0, atol=1e-10 * max(1.0, np.abs(g0).max()))
+    assert abs(e - oracle.energy(14, gates, th, terms)) <= 1e-10 * max(1.0, abs(e))
+    for i in (0, len(th) - 1):
+        p = th.copy()
+        p[i] += np.pi / 2
+        ep = oracle.energy(14, gates, p, terms)
+        p[i] -= np.pi
+        em = oracle.energy(14, gates, p, terms)
+        assert abs(g[i] - 0.5 * (ep - em)) <= 1e-10 * max(1.0, abs(g[i]))
+
+
+def test_autotune_uneven_batch(lq):
+    inst = W.uneven_batch(count=12, seed=9)
+    probs = [lq.BatchProblem(n, g, th, t) for n, g, th, t in inst]
+    r = lq.autotune_batch(probs)
+    big = any(n > 12 for n, _, _, _ in inst)
+    assert r["candidates"] == (4 if big else 1)
+    lq.batch_param_shift(probs)
+    for i, (n, g, th, t) in enumerate(inst):
+        if n <= 9:
+            e_w, g_w = oracle.param_shift(n, g, th, t)
+            assert abs(probs[i].energy - e_w) <= 1e-10 * max(1.0, abs(e_w))
+            np.testing.assert_allclose(probs[i].grad, g_w, rtol=0,
+                                       atol=1e-10 * max(1.0, np.abs(g_w).max()))
+    # a batch of small states has nothing to tune
+    small = [lq.BatchProblem(n, g, th, t) for n, g, th, t in inst if n <= 12][:3]
+    assert lq.autotune_batch(small)["candidates"] == 1
