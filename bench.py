@@ -188,6 +188,7 @@ class Step:
         # schedule autotuning of the layer (set-up, untimed): apply_circuit then
         # uses the chosen tile width / low bits / phase-table option
         self.tune = lq.autotune(n, self.layer, self.theta, scratch=self.work)
+        self.tune_qft = lq.autotune_qft(n, inverse=True, scratch=self.work)
         self.exp_ws = torch.empty(lq.load().lq_expval_workspace_size(n, len(self.terms)),
                                   dtype=torch.uint8, device=device)
         self.e_dev = torch.zeros(1, dtype=torch.float64, device=device)
@@ -205,7 +206,7 @@ class Step:
             self.has_adjoint = False
         plan_l = lq.circuit_plan(n, self.layer, self.theta)
         plan_f = lq.qft_plan(n, lq.QFT_FFT)
-        plan_g = lq.qft_plan(n, lq.QFT_GATES)
+        plan_g = lq.qft_plan(n, lq.QFT_GATES, inverse=True)
         plan_e = lq.expval_plan(n, self.terms)
         N = float(1 << n)
         self.rows = {
@@ -379,6 +380,7 @@ def bench_lq(a, rank, world, device):
         "hbm_frac": round(value / hbm_peak, 4),
         "rows": rows, "kernels": kernels, "roofline": roofline,
         "autotune_hea_layer": step.tune,
+        "autotune_qft_gates_inverse": step.tune_qft,
         "gpu_launches": launches * a.steps,
         "clocks": clk,
     }

@@ -253,8 +253,9 @@ typedef struct {
 lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* params, int np,
                           lq_plan_info* out);
 
-/* Plan of lq_qft (host only). */
+/* Plan of lq_qft (host only): the forward transform, or either direction. */
 lq_status lq_qft_plan(int n, int method, lq_plan_info* out);
+lq_status lq_qft_plan_dir(int n, int method, int inverse, lq_plan_info* out);
 
 /* ---------------------------------------------------------------------------
  * Schedule autotuner (no counterpart in the paper, whose CPU library has no
@@ -282,6 +283,11 @@ typedef struct {
 lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng,
                               const double* params, int np, lq_tune_result* out,
                               lq_stream stream);
+/* Autotune the gate form of lq_qft (its H / CP gate list, forward or
+ * inverse) like lq_autotune_circuit; lq_qft(method = LQ_QFT_GATES) then uses
+ * the recorded schedule. */
+lq_status lq_autotune_qft(void* scratch, int n, int inverse, lq_tune_result* out,
+                          lq_stream stream);
 lq_status lq_tune_cache_save(const char* path);
 lq_status lq_tune_cache_load(const char* path);
 lq_status lq_tune_cache_clear(void);

@@ -94,12 +94,12 @@ EXPORTS = [
     "lq_apply_pauli_sum", "lq_param_shift_workspace_size", "lq_param_shift_grad",
     "lq_param_shift_general_workspace_size", "lq_param_shift_grad_general",
     "lq_adjoint_workspace_size", "lq_adjoint_grad", "lq_trotter_evolve",
-    "lq_batch_workspace_size", "lq_batch_param_shift", "lq_circuit_plan", "lq_qft_plan",
+    "lq_batch_workspace_size", "lq_batch_param_shift", "lq_circuit_plan", "lq_qft_plan", "lq_qft_plan_dir",
     "lq_expval_pauli_sum_noalloc", "lq_server_footprint", "lq_server_create",
     "lq_server_submit", "lq_server_wait", "lq_server_destroy", "lq_vqe_workspace_size",
     "lq_vqe_adam", "lq_adjoint_plan", "lq_expval_plan", "lq_autotune_circuit",
     "lq_tune_cache_save", "lq_tune_cache_load", "lq_tune_cache_clear", "lq_tune_cache_size",
-    "lq_autotune_batch", "lq_autotune_param_shift",
+    "lq_autotune_batch", "lq_autotune_param_shift", "lq_autotune_qft",
 ]
 
 
@@ -167,6 +167,7 @@ def load(build_if_missing=True):
     L.lq_circuit_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
                                   P(LqPlanInfo)]
     L.lq_qft_plan.argtypes = [ctypes.c_int, ctypes.c_int, P(LqPlanInfo)]
+    L.lq_qft_plan_dir.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P(LqPlanInfo)]
     L.lq_expval_plan.argtypes = [ctypes.c_int, P(LqPauliTerm), ctypes.c_int, P(LqPlanInfo)]
     L.lq_autotune_circuit.argtypes = [c_void_p, ctypes.c_int, P(LqGate), ctypes.c_int,
                                       P(c_double), ctypes.c_int, P(LqTuneResult), c_void_p]
@@ -175,6 +176,7 @@ def load(build_if_missing=True):
     L.lq_autotune_param_shift.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double),
                                           ctypes.c_int, P(LqPauliTerm), ctypes.c_int, c_void_p,
                                           c_size_t, P(LqTuneResult), c_void_p]
+    L.lq_autotune_qft.argtypes = [c_void_p, ctypes.c_int, ctypes.c_int, P(LqTuneResult), c_void_p]
     L.lq_tune_cache_save.argtypes = [ctypes.c_char_p]
     L.lq_tune_cache_load.argtypes = [ctypes.c_char_p]
     L.lq_tune_cache_clear.argtypes = []
@@ -437,6 +439,18 @@ def autotune_param_shift(n, gates, params, terms, device="cuda", stream=None, wo
     return _tune_dict(r)
 
 
+def autotune_qft(n, inverse=False, scratch=None, stream=None):
+    """Pick the schedule of the gate-form QFT (forward or inverse) on this
+    GPU; qft(..., method=QFT_GATES) then uses it."""
+    if scratch is None:
+        scratch = new_state(n)
+    _check_state(scratch, n)
+    r = LqTuneResult()
+    _check(load().lq_autotune_qft(_ptr(scratch), n, int(inverse), ctypes.byref(r),
+                                  _stream(stream)))
+    return _tune_dict(r)
+
+
 def tune_cache_save(path):
     _check(load().lq_tune_cache_save(os.fsencode(path)))
 
@@ -462,9 +476,9 @@ def expval_plan(n, terms):
                 dram_bytes=info.dram_bytes)
 
 
-def qft_plan(n, method=QFT_FFT):
+def qft_plan(n, method=QFT_FFT, inverse=False):
     info = LqPlanInfo()
-    _check(load().lq_qft_plan(n, int(method), ctypes.byref(info)))
+    _check(load().lq_qft_plan_dir(n, int(method), int(inverse), ctypes.byref(info)))
     return dict(npasses=info.npasses, tile_bits=info.tile_bits, dp_flops=info.dp_flops,
                 dram_bytes=info.dram_bytes)
 

@@ -345,6 +345,13 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
       l.cm = cmbits ? ((1ull << cmbits) - 1) : 0;
       fl += op_flops(l, n);
     }
+    // deferred per-tile phases: one complex multiply per amplitude after the
+    // load and/or at the store
+    if (P.h.flags & PF_DFULL) {
+      const uint32_t all = (1u << P.h.ndefer) - 1u;
+      if (P.h.dpre) fl += 6.0 * std::ldexp(1.0, n);
+      if (all & ~(uint32_t)P.h.dpre) fl += 6.0 * std::ldexp(1.0, n);
+    }
   }
   out->dp_flops = fl;
   out->dram_bytes = 32.0 * std::ldexp(1.0, n) * S.npasses;

@@ -436,7 +436,8 @@ double op_flops(const LOp& o, int n) {
     case OP_PARITY: return 6.0 * N * 0.5 * frac;
     case OP_SCALE: return ((o.mode & 1) ? 2.0 : 6.0) * N;
     case OP_GRAD: return 4.0 * N;
-    case OP_DPHASE: return 12.0 * N * frac;                // table combine + multiply
+    case OP_DPHASE:                                        // (table combine +) multiply
+      return ((o.mode & DP_FULL) ? 6.0 : 12.0) * N * frac;
     case OP_LPHASE:                                        // (table combine +) multiply
       return ((o.mode & LP_TABLE) ? 6.0 : 12.0) * N * frac;
     default: return 0.0;                                   // sign flips, i^k, swaps
@@ -497,6 +498,16 @@ static void fill_lphase(double* pool, const LOp& s, uint64_t tile, const int* po
     pool[5 * f + 2] = bitsd(cv & ~tile);
     pool[5 * f + 3] = bitsd(s.dfac[4 * f + 2]);
     pool[5 * f + 4] = bitsd(s.dfac[4 * f + 3]);
+  }
+}
+
+// Tile-local bits an op mixes (pairs or quads of amplitudes differing in them).
+static uint32_t op_mixing_bits(const Op& d) {
+  switch (d.type) {
+    case OP_PAULI: case OP_GRAD: return d.x_loc;
+    case OP_H: case OP_PAIR_GEN: return 1u << d.b0;
+    case OP_QUAD_GEN: case OP_SWAP: return (1u << d.b0) | (1u << d.b1);
+    default: return 0;   // diagonal ops
   }
 }
 
@@ -671,6 +682,65 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
       if (words) {
         P.h.flags |= PF_DTAB;
         P.h.dtab_words = (int32_t)words;
+      }
+      // full tables with the per-tile phases deferred to the store or the load;
+      // a full-mode op's partial sums are built in the (still unused) tile
+      // buffer, so only its CTA-decided factor triples stay resident
+      int entries = 0, nd = 0;
+      uint32_t ubits = 0;
+      const int scratch_slots = (2 << k) / 256;   // 256-word tables the tile buffer holds
+      for (int o = 0; o < cnt && (P.h.flags & PF_DTAB); o++) {
+        Op& d = P.ops[o];
+        if (d.type != OP_DPHASE || !(d.mode & DP_TABLE) || nd == 8 || nd >= scratch_slots)
+          continue;
+        const int c = __builtin_popcount(d.cm_loc);
+        if (c < 1) continue;
+        const int sz = 1 << (k - c);
+        if (entries + sz > DFULL_MAX_ENTRIES || __builtin_popcount(ubits | d.cm_loc) > 6) continue;
+        // the per-tile part commutes to the store if no later op of the pass
+        // mixes a condition bit, else to the load if no earlier op does
+        bool later = false, earlier = false;
+        for (int o2 = o + 1; o2 < cnt; o2++) later |= (op_mixing_bits(P.ops[o2]) & d.cm_loc) != 0;
+        for (int o2 = 0; o2 < o; o2++) earlier |= (op_mixing_bits(P.ops[o2]) & d.cm_loc) != 0;
+        if (later && earlier) continue;
+        d.mode |= DP_FULL;
+        if (later) {
+          d.mode |= DP_PRE;
+          P.h.dpre |= (uint8_t)(1u << nd);
+        }
+        d.z_glob = (uint64_t)entries;
+        d.b0 = (uint8_t)nd;
+        entries += sz;
+        ubits |= d.cm_loc;
+        nd++;
+      }
+      if (nd) {
+        // re-lay the resident area: full-mode ops keep their triples only
+        uint32_t w2 = 0;
+        for (int o = 0; o < cnt; o++) {
+          Op& d = P.ops[o];
+          if (d.type != OP_DPHASE || !(d.mode & DP_TABLE)) continue;
+          d.z_loc = w2;
+          w2 += ((d.mode & DP_FULL) ? 0u : 256u) + 3u * d.b1;
+        }
+        P.h.dtab_words = (int32_t)w2;
+        P.h.flags |= PF_DFULL;
+        P.h.dfull_entries = entries;
+        P.h.ndefer = (int8_t)nd;
+        int nb = 0;
+        for (uint32_t u = ubits; u; u &= u - 1) P.h.dbits[nb++] = (int8_t)__builtin_ctz(u);
+        P.h.ndbits = (int8_t)nb;
+        auto squeeze = [&](uint32_t v) {   // bits of v at dbits -> index bits
+          uint32_t r = 0;
+          for (int i = 0; i < nb; i++) r |= ((v >> P.h.dbits[i]) & 1u) << i;
+          return (uint8_t)r;
+        };
+        for (int o = 0; o < cnt; o++) {
+          const Op& d = P.ops[o];
+          if (d.type != OP_DPHASE || !(d.mode & DP_FULL)) continue;
+          P.h.dmask[d.b0] = squeeze(d.cm_loc);
+          P.h.dval[d.b0] = squeeze(d.cv_loc);
+        }
       }
     }
     if (p + 1 == passes.size() && need_scale) {

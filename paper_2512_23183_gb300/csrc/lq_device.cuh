@@ -293,14 +293,16 @@ __device__ __forceinline__ void diag_apply(double2* __restrict__ sm, uint32_t cn
   }
 }
 
-// Per-CTA tables of a table-mode OP_DPHASE at `out`: words 0..255 the two
+// Per-CTA tables of a table-mode OP_DPHASE: at `out` (256 words) the two
 // 128-entry partial sums of the tile-bit weights (entry 0 of the first also
-// holds the weights that hold on every tile), then (CTA mask, CTA value,
-// weight) of each factor decided by CTA bits alone.  A factor that needs
+// holds the weights that hold on every tile); at `triples` (CTA mask, CTA
+// value, weight) of each factor decided by CTA bits alone.  A factor that needs
 // s_b = 0 adds w to the constant and -w to c_b.  All threads call it; it
 // ends with a barrier.
 template <int BLOCK>
-__device__ __forceinline__ void build_dphase_table(unsigned long long* out, int k, const Op& op,
+__device__ __forceinline__ void build_dphase_table(unsigned long long* out,
+                                                   unsigned long long* triples, int k,
+                                                   const Op& op,
                                                    const double* __restrict__ coef) {
   __shared__ unsigned long long dt_c[MAX_TILE_BITS + 1];
   const uint32_t tid = threadIdx.x;
@@ -342,26 +344,72 @@ __device__ __forceinline__ void build_dphase_table(unsigned long long* out, int 
       const uint64_t loc = (uint64_t)__double_as_longlong(F[4 * f]);
       const uint64_t gm = (uint64_t)__double_as_longlong(F[4 * f + 1]);
       if (((uint32_t)loc & ~op.cm_loc) != 0 || gm == 0) continue;
-      out[256 + 3 * q] = gm;
-      out[256 + 3 * q + 1] = (uint64_t)__double_as_longlong(F[4 * f + 2]);
-      out[256 + 3 * q + 2] = (unsigned long long)__double_as_longlong(F[4 * f + 3]);
+      triples[3 * q] = gm;
+      triples[3 * q + 1] = (uint64_t)__double_as_longlong(F[4 * f + 2]);
+      triples[3 * q + 2] = (unsigned long long)__double_as_longlong(F[4 * f + 3]);
       q++;
     }
   }
   __syncthreads();
 }
 
+// exp(2 pi i E / 2^34) from the two-level dyadic tables dtab (hi: 2^17
+// entries exp(2 pi i h / 2^17), lo: 2^17 entries exp(2 pi i l / 2^34)).
+__device__ __forceinline__ double2 dyadic_phase(unsigned long long E,
+                                                const double2* __restrict__ dtab) {
+  if (E == 0) return make_double2(1.0, 0.0);
+  double2 w = dtab[E >> DYADIC_HALF];
+  const unsigned long long lo = E & ((1ull << DYADIC_HALF) - 1ull);
+  if (lo) {
+    const double2 wl = dtab[(1u << DYADIC_HALF) + lo];
+    w = cmul(w, wl.x, wl.y);
+  }
+  return w;
+}
+
+// Full phase table of a full-mode OP_DPHASE: F[u] = exp(2 pi i (t0 + t1) /
+// 2^34) at s = expand(u, cm, cv), from its partial-sum tables tb (the
+// tile-invariant part of E).  No barrier: the caller synchronises.
+template <int BLOCK>
+__device__ __forceinline__ void build_dfull_table(double2* F, int k, const Op& op,
+                                                  const unsigned long long* tb,
+                                                  const double2* __restrict__ dtab) {
+  const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull;
+  const uint32_t cnt = 1u << (k - __popc(op.cm_loc));
+  for (uint32_t u = threadIdx.x; u < cnt; u += BLOCK) {
+    const uint32_t s = expand(u, op.cm_loc, op.cv_loc);
+    F[u] = dyadic_phase((tb[s & 127] + tb[128 + ((s >> 7) & 127)]) & M34, dtab);
+  }
+}
+
+// Per-tile constant of a table-mode OP_DPHASE: the sum of the weights of its
+// `ncta` CTA-decided factors (triples at tr) that hold for the tile's CTA
+// bits `base`; every warp computes it with shuffles.
+__device__ __forceinline__ unsigned long long dphase_tile_sum(const unsigned long long* tr,
+                                                              int ncta, uint64_t base) {
+  unsigned long long e0 = 0;
+  for (int q = (int)(threadIdx.x & 31); q < ncta; q += 32)
+    if ((base & tr[3 * q]) == tr[3 * q + 1]) e0 += tr[3 * q + 2];
+  for (int o = 16; o > 0; o >>= 1) e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+  return e0;
+}
+
+// Per-CTA tables of a pass (pass_kernel); a member is nullptr when absent.
+struct PassTables {
+  const double2* ltab;               // table-mode OP_LPHASE phase table
+  const unsigned long long* dpt;     // table-mode OP_DPHASE partial sums
+  const double2* dfull;              // full-mode OP_DPHASE phase tables
+  unsigned long long* dfe;           // full mode: this tile's deferred sums
+};
+
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
-// are `base`; dtab: dyadic phase tables (hi: 2^17 entries exp(2 pi i h / 2^17),
-// lo: 2^17 entries exp(2 pi i l / 2^34)); ltab: the pass's per-CTA phase
-// table (table-mode OP_LPHASE), or nullptr; dpt: the pass's per-CTA dyadic
-// tables (table-mode OP_DPHASE), or nullptr.
+// are `base`; dtab: the dyadic phase tables; tabs: the pass's per-CTA tables
+// (pass_kernel), or nullptr.
 template <int BLOCK>
 __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, const Op& op,
                                          const double* __restrict__ coef, uint64_t base,
                                          const double2* __restrict__ dtab,
-                                         const double2* __restrict__ ltab = nullptr,
-                                         const unsigned long long* __restrict__ dpt = nullptr) {
+                                         const PassTables* tabs = nullptr) {
   const uint32_t tid = threadIdx.x;
   // per-tile tables of OP_DPHASE (2 x 128 sums) or OP_LPHASE (2 x 128
   // phases); one op at a time uses it
@@ -570,13 +618,34 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       const double* F = coef + op.cidx;
       const uint32_t cnt = T >> __popc(cm);
       const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull, LOMASK = (1ull << DYADIC_HALF) - 1ull;
-      if ((op.mode & DP_TABLE) && dpt) {
+      if ((op.mode & DP_TABLE) && tabs && tabs->dpt) {
+        const unsigned long long* tb = tabs->dpt + op.z_loc;
+        if ((op.mode & DP_FULL) && tabs->dfull) {
+          // tile-invariant part from the full table; e0 deferred to the store
+          // (summed here) or to the load (summed when the tile started)
+          if (!(op.mode & DP_PRE)) {
+            const unsigned long long e0 = dphase_tile_sum(tb, (int)op.b1, base);   // triples
+            if (tid == 0) tabs->dfe[op.b0] = e0;
+          }
+          const double2* __restrict__ F = tabs->dfull + op.z_glob;
+          if ((cnt & (2 * BLOCK - 1)) == 0) {
+            for (uint32_t j = tid; j < cnt; j += 2 * BLOCK) {
+              const uint32_t s0 = expand(j, cm, cv), s1 = expand(j + BLOCK, cm, cv);
+              const double2 a = sm[s0], b = sm[s1], w0 = F[j], w1 = F[j + BLOCK];
+              sm[s0] = cmul(a, w0.x, w0.y);
+              sm[s1] = cmul(b, w1.x, w1.y);
+            }
+          } else {
+            for (uint32_t j = tid; j < cnt; j += BLOCK) {
+              const uint32_t s = expand(j, cm, cv);
+              const double2 w = F[j];
+              sm[s] = cmul(sm[s], w.x, w.y);
+            }
+          }
+          break;
+        }
         // per-CTA partial sums; the per-tile constant summed by each warp
-        const unsigned long long* tb = dpt + op.z_loc;
-        unsigned long long e0 = 0;
-        for (int q = (int)(tid & 31); q < (int)op.b1; q += 32)
-          if ((base & tb[256 + 3 * q]) == tb[256 + 3 * q + 1]) e0 += tb[256 + 3 * q + 2];
-        for (int o = 16; o > 0; o >>= 1) e0 += __shfl_xor_sync(0xffffffffu, e0, o);
+        const unsigned long long e0 = dphase_tile_sum(tb + 256, (int)op.b1, base);
         for (uint32_t j = tid; j < cnt; j += BLOCK) {
           const uint32_t s = expand(j, cm, cv);
           const unsigned long long e = (e0 + tb[s & 127] + tb[128 + ((s >> 7) & 127)]) & M34;
@@ -666,7 +735,8 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
       break;
     }
     case OP_LPHASE: {
-      if ((op.mode & LP_TABLE) && ltab) {
+      if ((op.mode & LP_TABLE) && tabs && tabs->ltab) {
+        const double2* __restrict__ ltab = tabs->ltab;
         diag_apply<BLOCK, 4>(sm, T >> __popc(cm), cm, cv, [&](uint32_t s, double2 v) {
           const double2 w = ltab[s];
           return cmul(v, w.x, w.y);

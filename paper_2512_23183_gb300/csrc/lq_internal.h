@@ -104,6 +104,13 @@ struct PassHeader {
   int32_t flags;          // PF_* below
   int32_t ltab_op;        // PF_LTAB: index of the table-mode OP_LPHASE
   int32_t dtab_words;     // PF_DTAB: 64-bit words of the per-CTA dyadic tables
+  int32_t dfull_entries;  // PF_DFULL: double2 entries of the per-CTA full phase tables
+  int8_t ndefer;          // PF_DFULL: deferred per-tile phase sums (<= 8)
+  int8_t ndbits;          // bits of the deferred phase table's index (<= 6)
+  int8_t dbits[6];        // their tile-local positions, ascending
+  uint8_t dmask[8], dval[8];   // per deferred sum: condition over the index bits
+  uint8_t dpre;           // deferred sums applied after the load (bit per slot);
+                          // the others are applied at the store
   uint64_t ntiles;        // 2^(n-k)
   const void* dtab;       // dyadic phase tables (device), set at launch
   int8_t tbits[16];       // tile-local bit j -> global bit position
@@ -116,6 +123,8 @@ enum PassFlags : int32_t {
   PF_LTAB = 8,            // ops[ltab_op] is a table-mode OP_LPHASE: its 2^k-entry
                           // phase table is built once per CTA (pass_kernel only)
   PF_DTAB = 16,           // some OP_DPHASE ops are in table mode (pass_kernel only)
+  PF_DFULL = 32,          // some table-mode OP_DPHASE ops use full phase tables and
+                          // defer their per-tile phases to the store (pass_kernel only)
 };
 
 // OP_DPHASE in table mode (Op::mode bit): every factor has at most one tile
@@ -127,6 +136,23 @@ enum PassFlags : int32_t {
 // decided by CTA bits alone, which each warp sums per tile with shuffles.
 constexpr uint8_t DP_TABLE = 0x80;
 constexpr uint32_t DTAB_MAX_WORDS = 4096;   // per pass (32 KiB of shared memory)
+
+// A table-mode OP_DPHASE in full mode (Op::mode bit): its tile-invariant
+// phase exp(2 pi i (t0 + t1) / 2^34) is one complex table over the op's free
+// tile bits (index = the op's loop index, at double2 offset z_glob of the
+// pass's full-table area), built once per CTA, so an affected amplitude costs
+// one complex multiply.  The per-tile part e0 is a phase on the amplitudes
+// meeting the op's condition; no later op of the pass mixes a condition bit,
+// so it commutes to the end of the pass: the op stores e0 in deferred slot b0,
+// and the store multiplies every amplitude by the phase of the sum of the
+// slots whose conditions (dmask, dval over the header's dbits) it meets.
+// When a later op mixes a condition bit but no earlier one does (the inverse
+// QFT: the phases of qubit i precede its H), e0 commutes to the start of the
+// pass instead (DP_PRE): it is summed when the tile starts and applied right
+// after the load.
+constexpr uint8_t DP_FULL = 0x40;
+constexpr uint8_t DP_PRE = 0x20;
+constexpr int DFULL_MAX_ENTRIES = 3072;     // per pass (48 KiB of shared memory)
 
 // OP_LPHASE in table mode (Op::mode bit): every factor's condition bit is a
 // tile bit, so phase(s) is the same for every tile and one 2^k-entry table,

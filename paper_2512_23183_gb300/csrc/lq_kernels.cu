@@ -80,6 +80,21 @@ const double2* dyadic_tables(cudaError_t* err) {
 // PF_LTAB, the phase table of the pass's table-mode OP_LPHASE (every factor
 // on a tile bit) is built once per CTA, after the tile buffers, and serves
 // every tile.
+// Deferred per-tile phase table of a pass: dD[v] = exp(2 pi i E(v) / 2^34),
+// E(v) = sum of the deferred sums (the pre-load ones, or the store ones) whose
+// conditions the index-bit pattern v meets.  No barrier.
+template <int BLOCK>
+__device__ __forceinline__ void build_deferred(double2* dD, const PassHeader& h,
+                                               const unsigned long long* dfe, bool pre) {
+  const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull;
+  for (uint32_t v = threadIdx.x; v < (1u << h.ndbits); v += BLOCK) {
+    unsigned long long E = 0;
+    for (int q = 0; q < h.ndefer; q++)
+      if ((((h.dpre >> q) & 1) != 0) == pre && (v & h.dmask[q]) == h.dval[q]) E += dfe[q];
+    dD[v] = dyadic_phase(E & M34, (const double2*)h.dtab);
+  }
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ PassParams P,
                                                         double2* __restrict__ state,
@@ -92,20 +107,42 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
   const int kh = k - m;
   for (uint32_t j = threadIdx.x; j < (1u << kh); j += BLOCK)
     hioff[j] = (uint32_t)(deposit(j, P.h.tbits + m, kh) >> m);
-  const double2* ltab = nullptr;
+  // dynamic shared memory: tile buffer(s), [phase table], [dyadic partial
+  // sums], [full dyadic phase tables]
+  __shared__ unsigned long long dfe[8];   // this tile's deferred dyadic sums
+  __shared__ double2 dD[64];              // this tile's deferred phase table
+  PassTables tabs = {nullptr, nullptr, nullptr, dfe};
+  double2* area = smem_tiles + (dbuf ? 2 * T : T);
   if (P.h.flags & PF_LTAB) {
-    double2* t = smem_tiles + (dbuf ? 2 * T : T);
-    build_lphase_table<BLOCK>(t, k, P.ops[P.h.ltab_op], P.coef);
-    ltab = t;
+    build_lphase_table<BLOCK>(area, k, P.ops[P.h.ltab_op], P.coef);
+    tabs.ltab = area;
+    area += T;
   }
-  const unsigned long long* dpt = nullptr;
+  // full-mode ops build their partial sums in the tile buffer (slot b0),
+  // which is not in use before the first tile
+  unsigned long long* scratch_tabs = reinterpret_cast<unsigned long long*>(smem_tiles);
   if (P.h.flags & PF_DTAB) {
-    unsigned long long* d = reinterpret_cast<unsigned long long*>(
-        smem_tiles + (dbuf ? 2 * T : T) + ((P.h.flags & PF_LTAB) ? T : 0));
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(area);
+    for (int o = 0; o < nops; o++) {
+      const Op& op = P.ops[o];
+      if (op.type != OP_DPHASE || !(op.mode & DP_TABLE)) continue;
+      if (op.mode & DP_FULL)
+        build_dphase_table<BLOCK>(scratch_tabs + 256 * op.b0, d + op.z_loc, k, op, P.coef);
+      else
+        build_dphase_table<BLOCK>(d + op.z_loc, d + op.z_loc + 256, k, op, P.coef);
+    }
+    tabs.dpt = d;
+    area += (P.h.dtab_words + 1) / 2;
+  }
+  const bool deferred = (P.h.flags & PF_DFULL) != 0;
+  // deferred sums applied at the store (the others after the load)
+  const bool post = deferred && ((((1u << P.h.ndefer) - 1u) & ~(uint32_t)P.h.dpre) != 0);
+  if (deferred) {
     for (int o = 0; o < nops; o++)
-      if (P.ops[o].type == OP_DPHASE && (P.ops[o].mode & DP_TABLE))
-        build_dphase_table<BLOCK>(d + P.ops[o].z_loc, k, P.ops[o], P.coef);
-    dpt = d;
+      if (P.ops[o].type == OP_DPHASE && (P.ops[o].mode & DP_FULL))
+        build_dfull_table<BLOCK>(area + P.ops[o].z_glob, k, P.ops[o],
+                                 scratch_tabs + 256 * P.ops[o].b0, (const double2*)P.h.dtab);
+    tabs.dfull = area;
   }
   const uint64_t ntiles = P.h.ntiles;
   const uint64_t total = ntiles * (uint64_t)nstates;
@@ -130,6 +167,7 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
     double2* __restrict__ sm = smem_tiles + (dbuf ? cur * T : 0);
     uint64_t base;
     double2* __restrict__ st = tile_of(w, &base);
+    if (threadIdx.x < 8) dfe[threadIdx.x] = 0;
     if (zero) {
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
         sm[s] = make_double2((base == 0 && s == 0) ? 1.0 : 0.0, 0.0);
@@ -145,13 +183,51 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
         sm[s] = st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)];
     }
     __syncthreads();
+    if (deferred && P.h.dpre) {
+      // per-tile parts hoisted to the load: warp w sums the (w mod 8)-th such ops
+      int wi = 0;
+      for (int o = 0; o < nops; o++) {
+        const Op& d = P.ops[o];
+        if (d.type != OP_DPHASE || !(d.mode & DP_PRE)) continue;
+        if ((int)(threadIdx.x >> 5) == (wi++ % (BLOCK / 32)) &&
+            (base & d.cm_glob) == d.cv_glob) {
+          const unsigned long long e0 = dphase_tile_sum(tabs.dpt + d.z_loc, (int)d.b1, base);
+          if ((threadIdx.x & 31) == 0) dfe[d.b0] = e0;
+        }
+      }
+      __syncthreads();
+      build_deferred<BLOCK>(dD, P.h, dfe, true);
+      __syncthreads();
+      const int nb = P.h.ndbits;
+      for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+        uint32_t idx = 0;
+        for (int i = 0; i < nb; i++) idx |= ((s >> P.h.dbits[i]) & 1u) << i;
+        const double2 wd = dD[idx];
+        sm[s] = cmul(sm[s], wd.x, wd.y);
+      }
+      __syncthreads();
+    }
     for (int o = 0; o < nops; o++) {
-      apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab, ltab, dpt);
+      apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab, &tabs);
+      __syncthreads();
+    }
+    if (post) {
+      build_deferred<BLOCK>(dD, P.h, dfe, false);
       __syncthreads();
     }
     if (store) {
-      for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
-        st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)] = sm[s];
+      if (post) {
+        const int nb = P.h.ndbits;
+        for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+          uint32_t idx = 0;
+          for (int i = 0; i < nb; i++) idx |= ((s >> P.h.dbits[i]) & 1u) << i;
+          const double2 w = dD[idx];
+          st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)] = cmul(sm[s], w.x, w.y);
+        }
+      } else {
+        for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
+          st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)] = sm[s];
+      }
     }
     __syncthreads();
   }
@@ -166,9 +242,10 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
   static bool configured = false;
   const size_t tile = sizeof(double2) << P.h.k;
   // double buffering for passes that load from HBM with tiles of <= 2^11
-  const int dbuf = (P.h.k <= 11 && !(P.h.flags & PF_INIT_ZERO)) ? 1 : 0;
+  const int dbuf = (P.h.k <= 11 && !(P.h.flags & (PF_INIT_ZERO | PF_DFULL))) ? 1 : 0;
   const size_t smem = tile * ((dbuf ? 2 : 1) + ((P.h.flags & PF_LTAB) ? 1 : 0)) +
-                      ((P.h.flags & PF_DTAB) ? sizeof(unsigned long long) * P.h.dtab_words : 0);
+                      ((P.h.flags & PF_DTAB) ? sizeof(double2) * ((P.h.dtab_words + 1) / 2) : 0) +
+                      ((P.h.flags & PF_DFULL) ? sizeof(double2) * P.h.dfull_entries : 0);
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(pass_kernel<kPassBlock>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,

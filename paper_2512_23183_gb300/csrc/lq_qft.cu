@@ -360,12 +360,12 @@ static std::vector<lq_gate> qft_gate_list(int n, int inverse) {
   return g;
 }
 
-extern "C" lq_status lq_qft_plan(int n, int method, lq_plan_info* out) {
+extern "C" lq_status lq_qft_plan_dir(int n, int method, int inverse, lq_plan_info* out) {
   lq_status st = check_n(n);
   if (st) return st;
   if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
   if (method == LQ_QFT_GATES) {
-    std::vector<lq_gate> g = qft_gate_list(n, 0);
+    std::vector<lq_gate> g = qft_gate_list(n, inverse);
     st = lq_circuit_plan(n, g.data(), (int)g.size(), nullptr, 0, out);
     if (st) return st;
     if (n > 1) {   // the bit-reversal pass
@@ -393,6 +393,18 @@ extern "C" lq_status lq_qft_plan(int n, int method, lq_plan_info* out) {
   out->dp_flops = fl;
   out->dram_bytes = 32.0 * N * (double)b.size();
   return LQ_OK;
+}
+
+extern "C" lq_status lq_qft_plan(int n, int method, lq_plan_info* out) {
+  return lq_qft_plan_dir(n, method, 0, out);
+}
+
+extern "C" lq_status lq_autotune_qft(void* scratch, int n, int inverse, lq_tune_result* out,
+                                     lq_stream stream) {
+  lq_status st = check_n(n);
+  if (st) return st;
+  std::vector<lq_gate> g = qft_gate_list(n, inverse);
+  return lq_autotune_circuit(scratch, n, g.data(), (int)g.size(), nullptr, 0, out, stream);
 }
 
 extern "C" lq_status lq_qft(void* amps, int n, int inverse, int method, void* scratch,

@@ -309,6 +309,34 @@ def test_trotter(lq, n, steps):
     np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
 
 
+@pytest.mark.parametrize("n,seed", [(12, 1), (15, 2), (17, 3), (20, 4)])
+def test_dyadic_runs_with_one_common_control(lq, n, seed):
+    # QFT-like blocks: H(i), then CP(i, j) on a random set of other qubits
+    # (one common control bit, phases deferred to the store or the load of
+    # the pass), sometimes with H(i) again after the run (the per-tile part
+    # must then stay in place or move to the load) or before the block's H
+    rng = np.random.default_rng(500 + seed)
+    gates = []
+    for _ in range(3 * n):
+        i = int(rng.integers(n))
+        if rng.random() < 0.3:
+            gates.append(W.G("H", i))
+        gates.append(W.G("H", i))
+        others = [j for j in range(n) if j != i]
+        for j in rng.choice(others, size=int(rng.integers(2, min(8, n - 1))), replace=False):
+            k = int(rng.integers(1, 25))
+            gates.append(W.G("CP", i, int(j), angle=float(rng.choice([1, -1]) * np.pi / 2 ** k)))
+        if rng.random() < 0.3:
+            gates.append(W.G("H", i))
+        if rng.random() < 0.2:
+            gates.append(W.G("RY", int(rng.integers(n)), angle=float(rng.uniform(-3, 3))))
+    psi = W.gaussian_state(n, 70 + seed)
+    want = oracle.apply_circuit(psi.copy(), n, gates)
+    t = dev(psi)
+    lq.apply_circuit(t, n, gates)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
+
+
 @pytest.mark.parametrize("n,seed", [(3, 1), (9, 2), (14, 3), (16, 4)])
 def test_fixed_dyadic_phase_runs(lq, n, seed):
     # runs of fixed dyadic diagonal gates (merged into one table-driven phase

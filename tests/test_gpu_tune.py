@@ -109,3 +109,18 @@ def test_autotune_uneven_batch(lq):
     # a batch of small states has nothing to tune
     small = [lq.BatchProblem(n, g, th, t) for n, g, th, t in inst if n <= 12][:3]
     assert lq.autotune_batch(small)["candidates"] == 1
+
+
+def test_autotune_qft_gate_form(lq):
+    import torch
+
+    n = 16
+    r = lq.autotune_qft(n, inverse=True)
+    assert r["ms"] <= r["ms_default"]
+    psi = W.gaussian_state(n, 21)
+    t = _dev(psi)
+    lq.qft(t, n, inverse=True, method=lq.QFT_GATES)
+    want = np.fft.fft(psi, norm="ortho")   # the inverse QFT: e^{-2 pi i xk/N} / sqrt(N)
+    np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
+    assert lq.qft_plan(n, lq.QFT_GATES)["npasses"] >= 2
+    del torch
