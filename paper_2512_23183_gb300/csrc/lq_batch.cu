@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
         const BPass& B = A.passes[P.pass_first + p];
         for (int o = 0; o < B.h.nops; o++) {
           const Op op = patched(A.ops[B.op_first + o], pt);
-          apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, 0, (const double2*)B.h.dtab);
+          apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, 0, (const double2*)B.h.dtab, nullptr,
+                          &pt);
           __syncthreads();
         }
       }
@@ -184,7 +185,8 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
           __syncthreads();
           for (int o = 0; o < B.h.nops; o++) {
             const Op op = patched(A.ops[B.op_first + o], pt);
-            apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, base, (const double2*)B.h.dtab);
+            apply_op<BLOCK>(sm, T, op, A.coef + B.coef_first, base, (const double2*)B.h.dtab,
+                            nullptr, &pt);
             __syncthreads();
           }
           for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
@@ -348,7 +350,9 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B,
     ScheduleOptions opt;
     opt.k = n <= BATCH_SMEM_BITS ? n : tile_bits;
     opt.force_scale = true;
-    opt.merge_params = false;   // shifted circuits patch individual gates
+    // one-bit phases of parametrised gates merge too: a shifted circuit's
+    // patch replaces its gate's factor when the kernel builds the tables
+    opt.merge_params = true;
     Schedule S;
     st = schedule_ops(n, ops, nops, zr, zi, opt, S);
     double flops = 0;
@@ -378,7 +382,7 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B,
         if (d.type == OP_PAIR_GEN) ncoef = std::max(ncoef, (int)d.cidx + 8);
         if (d.type == OP_QUAD_GEN) ncoef = std::max(ncoef, (int)d.cidx + 32);
         if (d.type == OP_DPHASE) ncoef = std::max(ncoef, (int)d.cidx + 4 * (int)d.x_loc);
-        if (d.type == OP_LPHASE) ncoef = std::max(ncoef, (int)d.cidx + 5 * (int)d.x_loc);
+        if (d.type == OP_LPHASE) ncoef = std::max(ncoef, (int)d.cidx + LPHASE_FAC * (int)d.x_loc);
       }
       for (int c = 0; c < ncoef; c++) B.coef.push_back(S.passes[p].coef[c]);
       B.passes.push_back(bp);

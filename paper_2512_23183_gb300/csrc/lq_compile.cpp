@@ -353,8 +353,9 @@ void merge_linear(std::vector<LOp>& ops, int n, bool params, std::vector<int>* s
       m.dfac.push_back(ops[k].cv);
       m.dfac.push_back(dbits_u(a));
       m.dfac.push_back(dbits_u(b));
+      m.dfac.push_back((uint64_t)(int64_t)ops[k].gate);   // for per-circuit patches
     }
-    m.ncoef = 5 * (int)(j - i);
+    m.ncoef = LPHASE_FAC * (int)(j - i);
     // merged: about 12 flops per amplitude plus per-tile tables
     if (j - i >= 3 && m.ncoef <= coef_budget && 13.0 * std::ldexp(1.0, n) < separate) {
       coef_budget -= m.ncoef;
@@ -487,17 +488,19 @@ static void fill_dphase(double* pool, const LOp& s, uint64_t tile, const int* po
 }
 
 // Factor list of an OP_LPHASE: per factor (tile-local cm | cv << 32, CTA cm,
-// CTA cv, re, im).
+// CTA cv, re, im, source gate index).
 static void fill_lphase(double* pool, const LOp& s, uint64_t tile, const int* pos) {
-  const std::size_t nf = s.dfac.size() / 4;
+  const std::size_t nf = s.dfac.size() / 5;
   for (std::size_t f = 0; f < nf; f++) {
-    uint64_t cm = s.dfac[4 * f], cv = s.dfac[4 * f + 1];
+    uint64_t cm = s.dfac[5 * f], cv = s.dfac[5 * f + 1];
     uint64_t loc = (uint64_t)to_local(cm & tile, pos) | ((uint64_t)to_local(cv & tile, pos) << 32);
-    pool[5 * f + 0] = bitsd(loc);
-    pool[5 * f + 1] = bitsd(cm & ~tile);
-    pool[5 * f + 2] = bitsd(cv & ~tile);
-    pool[5 * f + 3] = bitsd(s.dfac[4 * f + 2]);
-    pool[5 * f + 4] = bitsd(s.dfac[4 * f + 3]);
+    double* q = pool + LPHASE_FAC * f;
+    q[0] = bitsd(loc);
+    q[1] = bitsd(cm & ~tile);
+    q[2] = bitsd(cv & ~tile);
+    q[3] = bitsd(s.dfac[5 * f + 2]);
+    q[4] = bitsd(s.dfac[5 * f + 3]);
+    q[5] = bitsd(s.dfac[5 * f + 4]);
   }
 }
 
@@ -529,7 +532,7 @@ static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef
   d.cm_glob = s.cm & ~tile;
   d.cv_glob = s.cv & ~tile;
   d.x_loc = s.type == OP_DPHASE   ? (uint32_t)(s.dfac.size() / 3)
-            : s.type == OP_LPHASE ? (uint32_t)(s.dfac.size() / 4)
+            : s.type == OP_LPHASE ? (uint32_t)(s.dfac.size() / 5)
                                   : to_local(s.x, pos);
   d.z_loc = to_local(s.z & tile, pos);
   d.z_glob = s.z & ~tile;
@@ -640,8 +643,8 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
         fill_lphase(P.coef + coef_at, l, B.tile, pos);
         if (opt.lphase_table && k <= LTAB_MAX_BITS && !(P.h.flags & PF_LTAB)) {
           bool local = true;   // every factor's condition on a tile bit (or none)
-          for (std::size_t f = 0; f < l.dfac.size() / 4; f++)
-            if (l.dfac[4 * f] & ~B.tile) local = false;
+          for (std::size_t f = 0; f < l.dfac.size() / 5; f++)
+            if (l.dfac[5 * f] & ~B.tile) local = false;
           if (local) {
             P.ops[cnt].mode |= LP_TABLE;
             P.h.flags |= PF_LTAB;

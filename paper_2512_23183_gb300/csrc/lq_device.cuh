@@ -234,9 +234,10 @@ __device__ __forceinline__ void build_lphase_table(double2* tab, int k, const Op
   if (tid <= (uint32_t)k) {
     double cr = 1, ci = 0;
     for (int f = 0; f < nf; f++) {
-      const uint64_t loc = (uint64_t)__double_as_longlong(F[5 * f]);
+      const double* Ff = F + LPHASE_FAC * f;
+      const uint64_t loc = (uint64_t)__double_as_longlong(Ff[0]);
       const uint32_t lm = (uint32_t)loc, lv = (uint32_t)(loc >> 32);
-      double wr = F[5 * f + 3], wi = F[5 * f + 4];
+      double wr = Ff[3], wi = Ff[4];
       if (lm == 0) {
         if (tid != (uint32_t)k) continue;
       } else {
@@ -404,12 +405,14 @@ struct PassTables {
 
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
 // are `base`; dtab: the dyadic phase tables; tabs: the pass's per-CTA tables
-// (pass_kernel), or nullptr.
+// (pass_kernel), or nullptr; pt: the circuit's patch (batched launches: the
+// patched gate's factor of a merged one-bit phase op), or nullptr.
 template <int BLOCK>
 __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, const Op& op,
                                          const double* __restrict__ coef, uint64_t base,
                                          const double2* __restrict__ dtab,
-                                         const PassTables* tabs = nullptr) {
+                                         const PassTables* tabs = nullptr,
+                                         const Patch* pt = nullptr) {
   const uint32_t tid = threadIdx.x;
   // per-tile tables of OP_DPHASE (2 x 128 sums) or OP_LPHASE (2 x 128
   // phases); one op at a time uses it
@@ -758,12 +761,17 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
         // thread b < k builds c_b; thread k builds e0
         double cr = 1, ci = 0;
         for (int f = 0; f < nf; f++) {
-          const uint64_t loc = (uint64_t)__double_as_longlong(F[5 * f]);
-          const uint64_t gm = (uint64_t)__double_as_longlong(F[5 * f + 1]);
-          const uint64_t gv = (uint64_t)__double_as_longlong(F[5 * f + 2]);
+          const double* Ff = F + LPHASE_FAC * f;
+          const uint64_t loc = (uint64_t)__double_as_longlong(Ff[0]);
+          const uint64_t gm = (uint64_t)__double_as_longlong(Ff[1]);
+          const uint64_t gv = (uint64_t)__double_as_longlong(Ff[2]);
           if ((base & gm) != gv) continue;
           const uint32_t lm = (uint32_t)loc, lv = (uint32_t)(loc >> 32);
-          double wr = F[5 * f + 3], wi = F[5 * f + 4];
+          double wr = Ff[3], wi = Ff[4];
+          if (pt && (int)__double_as_longlong(Ff[5]) == pt->gate) {   // shifted circuit
+            wr = pt->a0;
+            wi = pt->b0;
+          }
           if (lm == 0) {
             if (tid != (uint32_t)k) continue;
           } else {

@@ -58,7 +58,7 @@ enum OpType : uint8_t {
                   // (x_loc factors at coef[cidx..], 4 doubles each)
   OP_LPHASE,      // merged one-bit phases: product of the unit factors w_f whose
                   // single condition bit holds (x_loc factors at coef[cidx..],
-                  // 5 doubles each)
+                  // LPHASE_FAC doubles each)
   OP_TYPE_COUNT
 };
 
@@ -91,6 +91,8 @@ struct Op {
 static_assert(sizeof(Op) == 64, "Op must stay 64 bytes");
 
 constexpr int DYADIC_BITS = 34;    // dyadic phases are multiples of 2 pi / 2^34
+constexpr int LPHASE_FAC = 6;      // doubles per OP_LPHASE factor: tile-local cm | cv << 32,
+                                   // CTA cm, CTA cv, re, im, source gate
 constexpr int DYADIC_HALF = 17;    // two-level table: 2^17 + 2^17 entries
 constexpr int MAX_TILE_BITS = 13;   // 2^13 amplitudes = 128 KiB of shared memory
 constexpr int MAX_OPS = 384;        // per pass (kernel-parameter budget)
