@@ -495,6 +495,20 @@ def vqe_extras(device):
     r["circuits_per_grad"] = 2 * P + 1
     res["adjoint_n24_d10_480p"] = r
     del psi, ws
+    # uneven batch: 64 instances (seed 4), n ~ U{8..20}, depth ~ U{2..12},
+    # ring HEA, random 50-term sums; every instance's energy and gradient in
+    # one persistent launch (one warm-up run, one timed)
+    inst = W.uneven_batch(count=64, seed=4)
+    probs = [lq.BatchProblem(n, g, th, t) for n, g, th, t in inst]
+    lq.batch_param_shift(probs, device=device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lq.batch_param_shift(probs, device=device)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ncirc = sum(2 * len(th) + 1 for _, _, th, _ in inst)
+    res["uneven_batch_64"] = {"s": round(dt, 3), "problem_grads_per_s": round(64 / dt, 3),
+                              "circuits": ncirc, "circuits_per_s": round(ncirc / dt, 1)}
     return res
 
 

@@ -45,7 +45,8 @@ namespace lq {
 static inline std::size_t align256(std::size_t b) { return (b + 255) & ~(std::size_t)255; }
 
 constexpr int BATCH_SMEM_BITS = 12;   // whole-state tiles up to n = 12
-constexpr int BATCH_TILE_BITS = 10;   // tile width of larger states
+constexpr int BATCH_TILE_BITS = 12;   // tile width of larger states (the autotuner's
+                                      // choice on the n = 16 and uneven batches)
 
 struct BPass {
   PassHeader h;
