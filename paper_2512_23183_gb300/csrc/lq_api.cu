@@ -255,7 +255,7 @@ lq_status lq_apply_circuit(void* amps, int n, const lq_gate* gates, int ng,
   LOp* ops = nullptr;
   std::size_t nops = 0;
   double zr, zi;
-  st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi);
+  st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi, true);
   if (st) return st;
   // the autotuner's choice for this (GPU, n, circuit structure), if any
   ScheduleOptions tuned;
@@ -321,7 +321,7 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
   LOp* ops = nullptr;
   std::size_t nops = 0;
   double zr, zi;
-  st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi);
+  st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi, true);
   if (st) return st;
   ScheduleOptions opt;
   opt.lphase_table = true;   // run by pass_kernel

@@ -253,7 +253,7 @@ static bool dyadic_diag(const LOp& o) {
   return o.fixed && o.dy >= 0 && (o.type == OP_PHASE || o.type == OP_SIGN || o.type == OP_MULI);
 }
 
-void merge_dyadic(std::vector<LOp>& ops, int n) {
+void merge_dyadic(std::vector<LOp>& ops, int n, bool full_tables) {
   std::vector<LOp> out;
   out.reserve(ops.size());
   std::size_t i = 0;
@@ -286,7 +286,11 @@ void merge_dyadic(std::vector<LOp>& ops, int n) {
       m.dfac.push_back((uint64_t)ops[k].dy);
     }
     m.ncoef = 4 * (int)(j - i);
-    if (j - i >= 2 && m.ncoef <= MAX_COEF / 2 && op_flops(m, n) < separate) {
+    // cost of the merged op: with per-CTA full tables (pass_kernel, a common
+    // control bit) one complex multiply per affected amplitude, else two
+    double merged = op_flops(m, n);
+    if (full_tables && cm) merged *= 0.5;
+    if (j - i >= 2 && m.ncoef <= MAX_COEF / 2 && merged < separate) {
       out.push_back(m);
     } else {
       for (std::size_t k = i; k < j; k++) out.push_back(ops[k]);
@@ -378,7 +382,8 @@ void merge_linear(std::vector<LOp>& ops, int n, bool params, std::vector<int>* s
 static const double kScaleLo = 1e-100, kScaleHi = 1e100;
 
 lq_status lower_circuit(int n, const lq_gate* gates, int ng, const double* params, int np,
-                        LOp** ops_out, std::size_t* nops_out, double* zr_out, double* zi_out) {
+                        LOp** ops_out, std::size_t* nops_out, double* zr_out, double* zi_out,
+                        bool full_tables) {
   lq_status st = check_gates(n, gates, ng, params, np);
   if (st) return st;
   std::vector<LOp> ops;
@@ -408,7 +413,7 @@ lq_status lower_circuit(int n, const lq_gate* gates, int ng, const double* param
       zi /= mag;
     }
   }
-  merge_dyadic(ops, n);
+  merge_dyadic(ops, n, full_tables);
   LOp* out = new LOp[ops.size() > 0 ? ops.size() : 1];
   for (std::size_t i = 0; i < ops.size(); i++) out[i] = ops[i];
   *ops_out = out;

@@ -246,16 +246,19 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
                        const ScheduleOptions& opt, Schedule& out);
 
 // Merge runs of fixed dyadic diagonal ops into OP_DPHASE, and runs of
-// one-bit phase ops into OP_LPHASE, where cheaper.  With params = false, ops
+// one-bit phase ops into OP_LPHASE, where cheaper (full_tables: the ops will
+// run in pass_kernel, where a dyadic op with a common control bit costs one
+// complex multiply per affected amplitude).  With params = false, ops
 // of parametrised gates are left alone (per-circuit patches address them).
-void merge_dyadic(std::vector<LOp>& ops, int n);
+void merge_dyadic(std::vector<LOp>& ops, int n, bool full_tables = false);
 void merge_linear(std::vector<LOp>& ops, int n, bool params, std::vector<int>* src,
                   int coef_budget);
 
 // Validate and lower a whole circuit at the given parameters.  The caller
 // owns *ops_out (delete[]).  (*zr, *zi) is the product of deferred factors.
 lq_status lower_circuit(int n, const lq_gate* gates, int ng, const double* params, int np,
-                        LOp** ops_out, std::size_t* nops_out, double* zr, double* zi);
+                        LOp** ops_out, std::size_t* nops_out, double* zr, double* zi,
+                        bool full_tables = false);
 
 // FP64 flops one op executes on a 2^n state (FMA = 2), in the op forms of the
 // tile kernels.

@@ -139,7 +139,7 @@ lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng
   LOp* ops = nullptr;
   std::size_t nops = 0;
   double zr, zi;
-  st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi);
+  st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi, true);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
