@@ -512,6 +512,51 @@ def vqe_extras(device):
     return res
 
 
+def next_rows_extras(device):
+    """The rows after the hot path: first-order Trotter evolution of the
+    time-dependent XYZ model (Sec. VII-A: J = 1, h(t) = 2 sin t, from
+    |1...1>) at n = 24 and 28, and the VQE Adam loop (Sec. VI-B settings:
+    lr 1e-2, at most 350 iterations, tolerance 1e-7) on the n = 10 depth-4
+    problem with adjoint and batched parameter-shift gradients."""
+    import numpy as np
+    import torch
+
+    import paper_2512_23183_gb300 as lq
+    import workloads as W
+
+    out = {}
+    dt, steps = 0.05, 20
+    for n in (24, 28):
+        static, field, A, om, x0 = W.xyz_trotter(n)
+        psi = lq.new_state(n, x0)
+        lq.trotter_evolve(psi, n, static, field, A, om, dt, 2)   # warm-up
+        lq.state_init(psi, n, x0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        lq.trotter_evolve(psi, n, static, field, A, om, dt, steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        # E(t) with the field at t = steps * dt
+        ht = A * np.sin(om * steps * dt)
+        e = lq.expval_pauli_sum(psi, n, static + [(c * ht, f) for c, f in field])
+        out["trotter_n%d" % n] = {"steps": steps, "dt": dt, "ms_per_step": round(ms / steps, 3),
+                                  "E_t": e}
+        del psi
+        torch.cuda.empty_cache()
+    gates, th, terms = W.vqe_chain(10, 4, 1)
+    for meth, name in ((0, "adjoint"), (1, "batched_psr")):
+        t0 = time.perf_counter()
+        p, es = lq.vqe_adam(10, gates, th, terms, method=meth)
+        dt_s = time.perf_counter() - t0
+        out["vqe_adam_n10_" + name] = {"iterations": int(es.size), "s": round(dt_s, 3),
+                                       "iters_per_s": round(es.size / dt_s, 1),
+                                       "E_first": float(es[0]), "E_last": float(es[-1])}
+    return out
+
+
 def qft_extras(device, sizes=(20, 24, 28, 30), reps=3):
     """The QFT workload as configured: FFT form and gate form at n = 20, 24,
     28, 30 on seeded Gaussian inputs, each timed with CUDA events (mean of
@@ -691,6 +736,8 @@ def main():
         if not a.no_extras:
             out["qft"] = qft_extras(device)
             out["vqe"] = vqe_extras(device)
+            torch.cuda.empty_cache()
+            out["next_rows"] = next_rows_extras(device)
             torch.cuda.empty_cache()
             out["serve"] = serve_extras(device)
         out["cpu_baseline"] = cpu_baseline(a.cpu_n)

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "lq_coefs.h"
+#include "lq_device.cuh"
 #include "lq_internal.h"
 #include "lq_kernels.h"
 
@@ -37,6 +38,171 @@ namespace lq {
                   __LINE__);                                                           \
     }                                                                                  \
   } while (0)
+
+static constexpr int kPassBlock = 256;
+
+// ------------------------------------------------------- two-state passes
+
+// Adjoint sweep: every op is applied to both tiles (psi in A, lambda in B);
+// an OP_GRAD op instead adds Im <lambda| G |psi> over its amplitudes
+// (G = condition projector x Pauli string: <i|P|j> = i^k0 (-1)^popcount(j & z),
+// j = i ^ x).  Each warp keeps its own running sum per gradient op of the
+// pass in shared memory (gacc[op][warp], no barrier, no global traffic per
+// tile); at the end the CTA adds the warp sums, in warp order, into
+// partial[slot * pstride + blockIdx.x] (one writer per entry, fixed
+// reduction order).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 4) pass2_kernel(const __grid_constant__ PassParams P,
+                                                      double2* __restrict__ psi,
+                                                      double2* __restrict__ lam,
+                                                      double* __restrict__ partial, int pstride,
+                                                      int ngrad) {
+  constexpr int NW = BLOCK / 32;
+  extern __shared__ double2 sm[];
+  __shared__ uint64_t hioff[256];
+  const int k = P.h.k, m = P.h.m, nops = P.h.nops;
+  const uint32_t T = 1u << k;
+  double2* A = sm;
+  double2* B = sm + T;
+  double* gacc = (double*)(sm + 2 * T);
+  const uint32_t lowmask = (1u << m) - 1u;
+  const int kh = k - m;
+  for (uint32_t j = threadIdx.x; j < (1u << kh); j += BLOCK)
+    hioff[j] = deposit(j, P.h.tbits + m, kh);
+  for (int j = threadIdx.x; j < ngrad * NW; j += BLOCK) gacc[j] = 0.0;
+  const uint64_t ntiles = P.h.ntiles;
+  const int warp = threadIdx.x >> 5;
+  __syncthreads();
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t base = deposit(t, P.h.obits, P.h.nobits);
+    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+      const uint64_t g = base | hioff[s >> m] | (s & lowmask);
+      A[s] = psi[g];
+      B[s] = lam[g];
+    }
+    __syncthreads();
+    int gl = 0;
+    for (int o = 0; o < nops; o++) {
+      const Op& op = P.ops[o];
+      if (op.type == OP_GRAD) {
+        double acc = 0.0;
+        if ((base & op.cm_glob) == op.cv_glob) {
+          const int zs = __popcll(base & op.z_glob) & 1;
+          const int k0 = op.mode & 3;
+          for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+            if ((s & op.cm_loc) != op.cv_loc) continue;
+            const uint32_t j = s ^ op.x_loc;
+            const int kk = (k0 + 2 * ((__popc(j & op.z_loc) + zs) & 1)) & 3;
+            const double2 v = mul_ipow(A[j], kk);
+            const double2 l = B[s];
+            acc = fma(l.x, v.y, fma(-l.y, v.x, acc));
+          }
+        }
+        for (int sh = 16; sh > 0; sh >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sh);
+        if ((threadIdx.x & 31) == 0) gacc[gl * NW + warp] += acc;
+        gl++;
+        // the next op may overwrite what this one read
+        if (o + 1 < nops && P.ops[o + 1].type != OP_GRAD) __syncthreads();
+      } else {
+        apply_op<BLOCK>(A, T, op, P.coef, base, (const double2*)P.h.dtab);
+        apply_op<BLOCK>(B, T, op, P.coef, base, (const double2*)P.h.dtab);
+        __syncthreads();
+      }
+    }
+    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+      const uint64_t g = base | hioff[s >> m] | (s & lowmask);
+      psi[g] = A[s];
+      lam[g] = B[s];
+    }
+    __syncthreads();
+  }
+  int gl = 0;
+  for (int o = 0; o < nops; o++) {
+    if (P.ops[o].type != OP_GRAD) continue;
+    if ((gl % BLOCK) == (int)threadIdx.x) {
+      double sum = 0.0;
+      for (int w = 0; w < NW; w++) sum += gacc[gl * NW + w];
+      partial[(uint64_t)P.ops[o].cidx * pstride + blockIdx.x] += sum;
+    }
+    gl++;
+  }
+}
+
+// Largest grid of a two-state pass (the stride of the partial sums): tiles
+// of 2^k amplitudes, up to 6 CTAs per SM.
+int pass2_grid(int n, int k) {
+  uint64_t ntiles = 1ull << (n - (k < n ? k : n));
+  size_t smem = 2 * (sizeof(double2) << (k < n ? k : n));
+  int per_sm = smem <= 32768 ? 6 : smem <= 65536 ? 3 : 1;
+  uint64_t cap = (uint64_t)sm_count() * per_sm;
+  return (int)(ntiles < cap ? ntiles : cap);
+}
+
+cudaError_t launch_pass2(const PassParams& P, double2* psi, double2* lam, double* partial,
+                         int grid, cudaStream_t s) {
+  (void)cudaGetLastError();  // report only this launcher's own errors
+  constexpr int NW = kPassBlock / 32;
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t ce = once_per_device(configured, [] {
+    // two tiles of at most 2^12 amplitudes and one running sum per warp per op
+    return cudaFuncSetAttribute(pass2_kernel<kPassBlock>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * (sizeof(double2) << 12) + sizeof(double) * NW * MAX_OPS));
+  });
+  if (ce != cudaSuccess) return ce;
+  if (P.h.k > 12) return cudaErrorInvalidValue;
+  int ngrad = 0;
+  for (int o = 0; o < P.h.nops; o++) ngrad += P.ops[o].type == OP_GRAD;
+  const size_t smem = 2 * (sizeof(double2) << P.h.k) + sizeof(double) * NW * ngrad;
+  // one wave of resident CTAs (registers and shared memory)
+  int per_sm = 0;
+  cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, pass2_kernel<kPassBlock>, kPassBlock, smem);
+  if (oe != cudaSuccess) return oe;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  uint64_t g = (uint64_t)sm_count() * per_sm;
+  if (g > P.h.ntiles) g = P.h.ntiles;
+  const int pgrid = (int)g < grid ? (int)g : grid;
+  if (P.h.flags & PF_DYADIC) {
+    cudaError_t e;
+    const double2* t = dyadic_tables(&e);
+    if (!t) return e;
+    static thread_local PassParams Q;
+    Q = P;
+    Q.h.dtab = t;
+    pass2_kernel<kPassBlock><<<pgrid, kPassBlock, smem, s>>>(Q, psi, lam, partial, grid, ngrad);
+  } else {
+    pass2_kernel<kPassBlock><<<pgrid, kPassBlock, smem, s>>>(P, psi, lam, partial, grid, ngrad);
+  }
+  return cudaGetLastError();
+}
+
+// grad[p] = sum over the slots of parameter p (in slot order) of
+// factor[slot] * sum_b partial[slot][b].
+__global__ void grad_reduce_kernel(const double* __restrict__ partial, int grid,
+                                   const double* __restrict__ factor,
+                                   const int* __restrict__ first, const int* __restrict__ count,
+                                   int np, double* __restrict__ grad) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  double g = 0;
+  for (int s = first[p]; s < first[p] + count[p]; s++) {
+    double v = 0;
+    for (int b = 0; b < grid; b++) v += partial[(uint64_t)s * grid + b];
+    g += factor[s] * v;
+  }
+  grad[p] = g;
+}
+
+cudaError_t launch_grad_reduce(const double* partial, int grid, const double* factor,
+                               const int* first, const int* count, int np, double* grad,
+                               cudaStream_t s) {
+  (void)cudaGetLastError();  // report only this launcher's own errors
+  if (np <= 0) return cudaSuccess;
+  grad_reduce_kernel<<<(np + 127) / 128, 128, 0, s>>>(partial, grid, factor, first, count, np,
+                                                      grad);
+  return cudaGetLastError();
+}
 
 static inline std::size_t align256(std::size_t b) { return (b + 255) & ~(std::size_t)255; }
 

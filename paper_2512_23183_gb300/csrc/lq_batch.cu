@@ -565,12 +565,11 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
   int dev = 0;
   LQ_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(LQ_ERR_INVALID_ARG, "device %d", dev);
-  static bool configured = false;
-  if (!configured) {
-    LQ_CUDA(cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(double2) << BATCH_SMEM_BITS)));
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  LQ_CUDA(once_per_device(configured, [] {
+    return cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double2) << BATCH_SMEM_BITS));
+  }));
   std::lock_guard<std::mutex> lock(g_graph_mu);
   if (!g_graph_stream[dev]) {
     LQ_CUDA(cudaStreamCreateWithFlags(&g_graph_stream[dev], cudaStreamNonBlocking));

@@ -456,15 +456,14 @@ cudaError_t launch_expval_tiled(const XPlan& X, const double2* states, uint64_t 
   const int nch = (X.n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS;
   const size_t smem = (sizeof(double2) << k) + sizeof(double2) * X.ncoef +
                       (X.tables ? sizeof(double) * 256 * nch : 0);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t ce = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(
         expval_tile_kernel<kXBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
         (int)((sizeof(double2) << XP_TILE_BITS) + sizeof(double2) * XP_MAX_COEF +
               sizeof(double) * 256 * ((34 + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS)));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  });
+  if (ce != cudaSuccess) return ce;
   // one wave of resident CTAs (the launch bound allows 4 per SM; shared
   // memory, with ~1.5 KiB static and 1 KiB reserved, may allow fewer)
   int per_sm = (int)((228u << 10) / (smem + (3u << 10)));

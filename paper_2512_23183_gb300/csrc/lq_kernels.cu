@@ -239,20 +239,18 @@ static constexpr int kPassBlock = 256;
 cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, int nstates,
                         cudaStream_t s) {
   (void)cudaGetLastError();  // report only this launcher's own errors
-  static bool configured = false;
+  static std::atomic<uint64_t> configured{0};
   const size_t tile = sizeof(double2) << P.h.k;
   // double buffering for passes that load from HBM with tiles of <= 2^11
   const int dbuf = (P.h.k <= 11 && !(P.h.flags & (PF_INIT_ZERO | PF_DFULL))) ? 1 : 0;
   const size_t smem = tile * ((dbuf ? 2 : 1) + ((P.h.flags & PF_LTAB) ? 1 : 0)) +
                       ((P.h.flags & PF_DTAB) ? sizeof(double2) * ((P.h.dtab_words + 1) / 2) : 0) +
                       ((P.h.flags & PF_DFULL) ? sizeof(double2) * P.h.dfull_entries : 0);
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(pass_kernel<kPassBlock>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(200u << 10));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t ce = once_per_device(configured, [] {
+    return cudaFuncSetAttribute(pass_kernel<kPassBlock>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200u << 10));
+  });
+  if (ce != cudaSuccess) return ce;
   uint64_t total = P.h.ntiles * (uint64_t)nstates;
   // resident CTAs per SM: the launch bound allows 4; shared memory (dynamic
   // + ~6 KiB static + 1 KiB reserved, of 228 KiB) may allow fewer
@@ -274,140 +272,6 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------- two-state passes
-
-// Adjoint sweep: every op is applied to both tiles (psi in A, lambda in B);
-// an OP_GRAD op instead adds Im <lambda| G |psi> over its amplitudes
-// (G = condition projector x Pauli string: <i|P|j> = i^k0 (-1)^popcount(j & z),
-// j = i ^ x) into partial[slot * gridDim.x + blockIdx.x] (one writer per
-// entry, fixed reduction order).
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) pass2_kernel(const __grid_constant__ PassParams P,
-                                                      double2* __restrict__ psi,
-                                                      double2* __restrict__ lam,
-                                                      double* __restrict__ partial) {
-  extern __shared__ double2 sm[];
-  __shared__ uint64_t hioff[256];
-  __shared__ double red[BLOCK / 32];
-  const int k = P.h.k, m = P.h.m, nops = P.h.nops;
-  const uint32_t T = 1u << k;
-  double2* A = sm;
-  double2* B = sm + T;
-  const uint32_t lowmask = (1u << m) - 1u;
-  const int kh = k - m;
-  for (uint32_t j = threadIdx.x; j < (1u << kh); j += BLOCK)
-    hioff[j] = deposit(j, P.h.tbits + m, kh);
-  const uint64_t ntiles = P.h.ntiles;
-  __syncthreads();
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint64_t base = deposit(t, P.h.obits, P.h.nobits);
-    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
-      const uint64_t g = base | hioff[s >> m] | (s & lowmask);
-      A[s] = psi[g];
-      B[s] = lam[g];
-    }
-    __syncthreads();
-    for (int o = 0; o < nops; o++) {
-      const Op& op = P.ops[o];
-      if (op.type == OP_GRAD) {
-        double acc = 0.0;
-        if ((base & op.cm_glob) == op.cv_glob) {
-          const int zs = __popcll(base & op.z_glob) & 1;
-          const int k0 = op.mode & 3;
-          for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
-            if ((s & op.cm_loc) != op.cv_loc) continue;
-            const uint32_t j = s ^ op.x_loc;
-            const int kk = (k0 + 2 * ((__popc(j & op.z_loc) + zs) & 1)) & 3;
-            const double2 v = mul_ipow(A[j], kk);
-            const double2 l = B[s];
-            acc = fma(l.x, v.y, fma(-l.y, v.x, acc));
-          }
-        }
-        for (int sh = 16; sh > 0; sh >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sh);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double sum = 0;
-          for (int w = 0; w < BLOCK / 32; w++) sum += red[w];
-          partial[(uint64_t)op.cidx * gridDim.x + blockIdx.x] += sum;
-        }
-      } else {
-        apply_op<BLOCK>(A, T, op, P.coef, base, (const double2*)P.h.dtab);
-        apply_op<BLOCK>(B, T, op, P.coef, base, (const double2*)P.h.dtab);
-      }
-      __syncthreads();
-    }
-    for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
-      const uint64_t g = base | hioff[s >> m] | (s & lowmask);
-      psi[g] = A[s];
-      lam[g] = B[s];
-    }
-    __syncthreads();
-  }
-}
-
-int pass2_grid(int n, int k) {
-  uint64_t ntiles = 1ull << (n - (k < n ? k : n));
-  size_t smem = 2 * (sizeof(double2) << (k < n ? k : n));
-  int per_sm = smem <= 32768 ? 6 : smem <= 65536 ? 3 : 1;
-  uint64_t cap = (uint64_t)sm_count() * per_sm;
-  return (int)(ntiles < cap ? ntiles : cap);
-}
-
-cudaError_t launch_pass2(const PassParams& P, double2* psi, double2* lam, double* partial,
-                         int grid, cudaStream_t s) {
-  (void)cudaGetLastError();  // report only this launcher's own errors
-  static bool configured = false;
-  if (!configured) {
-    // two tiles of at most 2^12 amplitudes (128 KiB)
-    cudaError_t e = cudaFuncSetAttribute(pass2_kernel<kPassBlock>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * (sizeof(double2) << 12)));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  if (P.h.k > 12) return cudaErrorInvalidValue;
-  size_t smem = 2 * (sizeof(double2) << P.h.k);
-  if (P.h.flags & PF_DYADIC) {
-    cudaError_t e;
-    const double2* t = dyadic_tables(&e);
-    if (!t) return e;
-    static thread_local PassParams Q;
-    Q = P;
-    Q.h.dtab = t;
-    pass2_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(Q, psi, lam, partial);
-  } else {
-    pass2_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, psi, lam, partial);
-  }
-  return cudaGetLastError();
-}
-
-// grad[p] = sum over the slots of parameter p (in slot order) of
-// factor[slot] * sum_b partial[slot][b].
-__global__ void grad_reduce_kernel(const double* __restrict__ partial, int grid,
-                                   const double* __restrict__ factor,
-                                   const int* __restrict__ first, const int* __restrict__ count,
-                                   int np, double* __restrict__ grad) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  double g = 0;
-  for (int s = first[p]; s < first[p] + count[p]; s++) {
-    double v = 0;
-    for (int b = 0; b < grid; b++) v += partial[(uint64_t)s * grid + b];
-    g += factor[s] * v;
-  }
-  grad[p] = g;
-}
-
-cudaError_t launch_grad_reduce(const double* partial, int grid, const double* factor,
-                               const int* first, const int* count, int np, double* grad,
-                               cudaStream_t s) {
-  (void)cudaGetLastError();  // report only this launcher's own errors
-  if (np <= 0) return cudaSuccess;
-  grad_reduce_kernel<<<(np + 127) / 128, 128, 0, s>>>(partial, grid, factor, first, count, np,
-                                                      grad);
-  return cudaGetLastError();
-}
 
 // ------------------------------------------------------------ Pauli sums
 

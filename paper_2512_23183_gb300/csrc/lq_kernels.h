@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <utility>
 #include <vector>
@@ -128,6 +129,20 @@ lq_status batch_run(const std::vector<HostProblem>& hps, void* ws, std::size_t w
 // states and records the fastest for this batch structure.
 lq_status batch_autotune(const std::vector<HostProblem>& hps, void* ws, std::size_t ws_bytes,
                          cudaStream_t s, lq_tune_result* res);
+
+// Run `set` (a kernel's cudaFuncSetAttribute calls) once per device; the
+// calling threads may race, the attribute calls are idempotent.
+template <typename F>
+cudaError_t once_per_device(std::atomic<uint64_t>& done, F set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // --------------------------------------------------------------- launchers
 

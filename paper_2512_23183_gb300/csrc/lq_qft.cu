@@ -197,9 +197,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F
 cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, double scale,
                             cudaStream_t s) {
   (void)cudaGetLastError();  // report only this launcher's own errors
-  static bool configured = false;
-  const int max_smem = (int)((sizeof(double2) << MAX_TILE_BITS) + (sizeof(double2) << FFT_MAX_D));
-  if (!configured) {
+  static std::atomic<uint64_t> configured{0};
+  cudaError_t ce = once_per_device(configured, [] {
+    const int max_smem = (int)((sizeof(double2) << MAX_TILE_BITS) + (sizeof(double2) << FFT_MAX_D));
     cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<256, 4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e == cudaSuccess)
@@ -208,9 +208,9 @@ cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, 
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fft_pass_kernel<1024, 1>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+    return e;
+  });
+  if (ce != cudaSuccess) return ce;
   FftParams F;
   F.n = n;
   F.q0 = q0;
@@ -289,14 +289,12 @@ __global__ void bitrev_small_kernel(double2* __restrict__ state, int n) {
 cudaError_t launch_bitrev(double2* state, int n, cudaStream_t s) {
   (void)cudaGetLastError();  // report only this launcher's own errors
   if (n <= 12) {
-    static bool conf = false;
-    if (!conf) {
-      cudaError_t e = cudaFuncSetAttribute(bitrev_small_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(sizeof(double2) << 12));
-      if (e != cudaSuccess) return e;
-      conf = true;
-    }
+    static std::atomic<uint64_t> conf{0};
+    cudaError_t ce = once_per_device(conf, [] {
+      return cudaFuncSetAttribute(bitrev_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(double2) << 12));
+    });
+    if (ce != cudaSuccess) return ce;
     bitrev_small_kernel<<<1, 512, sizeof(double2) << n, s>>>(state, n);
     return cudaGetLastError();
   }
