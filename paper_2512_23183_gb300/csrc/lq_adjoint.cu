@@ -43,6 +43,72 @@ static constexpr int kPassBlock = 256;
 
 // ------------------------------------------------------- two-state passes
 
+// Gradient terms of a run of diagonal generators G_t (Z strings z_t under
+// conditions cm_t/cv_t; x = 0, no factor i) on the two tiles A = psi,
+// B = lambda: Im <lambda|G_t|psi> = sum_s G_t(s) q_s with
+// q_s = Im(conj(lambda_s) psi_s).  Diagonal unitaries applied to both states
+// leave q unchanged, which is why a run of diagonal gates of the reverse
+// sweep can take all its gradients at one point.  A thread holds the
+// amplitudes s = tid + i * BLOCK (i < 8, T <= 8 * BLOCK); after a Walsh-
+// Hadamard transform over i, W[m] = sum_i (-1)^popcount(i & m) q_i, so
+//   sum_s (-1)^popcount(s & M) q_s = (-1)^popcount(tid & M) W[M / BLOCK]
+// over this thread's amplitudes, and a condition on the bits cm with values
+// cv expands as prod_b (1 + (-1)^(s_b + cv_b)) / 2 over its bits:
+//   sum_s [cond(s)] (-1)^popcount(s & z) q_s
+//     = 2^-|cm| sum_{S subset of cm} (-1)^popcount(cv & S) W(z ^ S).
+// Each term's CTA sum is added (by lane 0 of each warp) to acc[t * stride].
+template <int BLOCK>
+__device__ __forceinline__ void diag_grad_terms(const double2* __restrict__ A,
+                                                const double2* __restrict__ B, uint32_t T,
+                                                const Op* ops, int nterms, uint64_t base,
+                                                double* acc, int stride) {
+  constexpr int LB = BLOCK == 1024 ? 10 : BLOCK == 512 ? 9 : BLOCK == 256 ? 8 : 7;
+  static_assert((1 << LB) == BLOCK, "BLOCK must be a power of two in 128..1024");
+  const uint32_t tid = threadIdx.x;
+  double q[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const uint32_t s = tid + (uint32_t)i * BLOCK;
+    q[i] = 0.0;
+    if (s < T) {
+      const double2 l = B[s], v = A[s];
+      q[i] = fma(l.x, v.y, -l.y * v.x);
+    }
+  }
+#pragma unroll
+  for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+      if (!(i & h)) {
+        const double a = q[i], b = q[i | h];
+        q[i] = a + b;
+        q[i | h] = a - b;
+      }
+  for (int t = 0; t < nterms; t++) {
+    const Op& d = ops[t];
+    double v = 0.0;
+    if ((base & d.cm_glob) == d.cv_glob) {
+      const uint32_t cm = d.cm_loc, cv = d.cv_loc;
+      uint32_t S = cm;
+      while (true) {
+        const uint32_t M = d.z_loc ^ S;
+        const uint32_t mi = (M >> LB) & 7u;
+        double w = q[0];
+#pragma unroll
+        for (int j = 1; j < 8; j++) w = (mi == (uint32_t)j) ? q[j] : w;
+        const int neg = (__popc(tid & M & (BLOCK - 1)) + __popc(cv & S)) & 1;
+        v += neg ? -w : w;
+        if (S == 0) break;
+        S = (S - 1) & cm;
+      }
+      v = ldexp(v, -__popc(cm));
+      if (__popcll(base & d.z_glob) & 1) v = -v;
+    }
+    for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+    if ((tid & 31) == 0) acc[t * stride] += v;
+  }
+}
+
 // Adjoint sweep: every op is applied to both tiles (psi in A, lambda in B);
 // an OP_GRAD op instead adds Im <lambda| G |psi> over its amplitudes
 // (G = condition projector x Pauli string: <i|P|j> = i^k0 (-1)^popcount(j & z),
@@ -52,7 +118,7 @@ static constexpr int kPassBlock = 256;
 // partial[slot * pstride + blockIdx.x] (one writer per entry, fixed
 // reduction order).
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 4) pass2_kernel(const __grid_constant__ PassParams P,
+__global__ void __launch_bounds__(BLOCK, 3) pass2_kernel(const __grid_constant__ PassParams P,
                                                       double2* __restrict__ psi,
                                                       double2* __restrict__ lam,
                                                       double* __restrict__ partial, int pstride,
@@ -84,7 +150,18 @@ __global__ void __launch_bounds__(BLOCK, 4) pass2_kernel(const __grid_constant__
     int gl = 0;
     for (int o = 0; o < nops; o++) {
       const Op& op = P.ops[o];
-      if (op.type == OP_GRAD) {
+      if (op.type == OP_GRAD && op.x_loc == 0 && (op.mode & 3) == 0 && T <= 8 * BLOCK) {
+        // a run of diagonal generators (Z strings under conditions): one
+        // pass over the tile for all of them (see diag_grad_terms)
+        int e = o + 1;
+        while (e < nops && P.ops[e].type == OP_GRAD && P.ops[e].x_loc == 0 &&
+               (P.ops[e].mode & 3) == 0)
+          e++;
+        diag_grad_terms<BLOCK>(A, B, T, P.ops + o, e - o, base, gacc + gl * NW + warp, NW);
+        gl += e - o;
+        o = e - 1;
+        if (e < nops && P.ops[e].type != OP_GRAD) __syncthreads();
+      } else if (op.type == OP_GRAD) {
         double acc = 0.0;
         if ((base & op.cm_glob) == op.cv_glob) {
           const int zs = __popcll(base & op.z_glob) & 1;
@@ -103,6 +180,10 @@ __global__ void __launch_bounds__(BLOCK, 4) pass2_kernel(const __grid_constant__
         gl++;
         // the next op may overwrite what this one read
         if (o + 1 < nops && P.ops[o + 1].type != OP_GRAD) __syncthreads();
+      } else if (op.type == OP_LPHASE && !(op.mode & LP_TABLE)) {
+        // the same per-tile phase tables serve both states
+        apply_op<BLOCK>(A, T, op, P.coef, base, (const double2*)P.h.dtab, nullptr, nullptr, B);
+        __syncthreads();
       } else {
         apply_op<BLOCK>(A, T, op, P.coef, base, (const double2*)P.h.dtab);
         apply_op<BLOCK>(B, T, op, P.coef, base, (const double2*)P.h.dtab);
@@ -128,8 +209,13 @@ __global__ void __launch_bounds__(BLOCK, 4) pass2_kernel(const __grid_constant__
   }
 }
 
+// Tile bits of the reverse sweep: two 32 KiB tiles per CTA (3 CTAs per SM)
+// measured 11% faster than 2^10-amplitude tiles at n = 24 (fewer passes).
+static int sweep_tile_bits(int n) { return n < 11 ? n : 11; }
+
 // Largest grid of a two-state pass (the stride of the partial sums): tiles
-// of 2^k amplitudes, up to 6 CTAs per SM.
+// of 2^k amplitudes, up to 6 CTAs per SM; passes with wider tiles launch
+// fewer CTAs.
 int pass2_grid(int n, int k) {
   uint64_t ntiles = 1ull << (n - (k < n ? k : n));
   size_t smem = 2 * (sizeof(double2) << (k < n ? k : n));
@@ -260,41 +346,60 @@ static LOp grad_op(const lq_gate& g, int n, double* fgen) {
 
 namespace lq {
 // The reverse sweep as scheduled tile passes: for k = L..1 an OP_GRAD op
-// (if gate k has a parameter), then the ops of U_k^dag.  factor[slot] is the
-// generator factor times |zeta|^2 at the gradient op's execution point.
+// (if gate k has a parameter), then the ops of U_k^dag.  Within a run of
+// diagonal gates (diagonal generators and inverses: RZ, P, CP, RZZ, CRZ and
+// the fixed phase gates) the gradient ops of the whole run come first: the
+// run's inverses are diagonal unitaries applied to both states, which leave
+// every Im(conj(lambda_s) psi_s) unchanged, so the gradients are the same at
+// any point of the run; the run's phase ops then stand next to each other
+// and merge into one op.  factor[slot] is the generator factor times
+// |zeta|^2 at the gradient op's execution point.
 static lq_status build_sweep(int n, const lq_gate* gates, int ng, const double* params,
                              std::vector<LOp>& ops, std::vector<double>& factor,
-                             std::vector<int>& slot_param, Schedule& S) {
+                             std::vector<int>& slot_param, Schedule& S, int tile_bits) {
   lq_status st;
   ops.clear();
   factor.clear();
   slot_param.clear();
   ops.reserve((std::size_t)ng * 2 + 8);
+  std::vector<LOp> run_grads, run_ops;   // the current run of diagonal gates
+  auto flush = [&]() {
+    ops.insert(ops.end(), run_grads.begin(), run_grads.end());
+    ops.insert(ops.end(), run_ops.begin(), run_ops.end());
+    run_grads.clear();
+    run_ops.clear();
+  };
   double zr = 1, zi = 0;
   for (int gi = ng - 1; gi >= 0; gi--) {
     const lq_gate& G = gates[gi];
     double th = G.angle + (G.param >= 0 ? params[G.param] : 0.0);
+    lq_gate inv = inverse_gate(G);
+    Lowered L;
+    st = lower_gate(inv, n, -th, L);
+    if (st) return st;
+    bool diagonal = true;
+    for (int j = 0; j < L.nops; j++) diagonal = diagonal && L.op[j].mix() == 0;
+    LOp go;
     if (G.param >= 0) {
       double fgen;
-      LOp go = grad_op(G, n, &fgen);
+      go = grad_op(G, n, &fgen);
       go.slot = (int)factor.size();
       go.gate = gi;
       go.a = fgen;   // the |zeta|^2 part is added in execution order below
       factor.push_back(fgen);
       slot_param.push_back(G.param);
-      ops.push_back(go);
+      diagonal = diagonal && go.x == 0;
     }
-    lq_gate inv = inverse_gate(G);
-    Lowered L;
-    st = lower_gate(inv, n, -th, L);
-    if (st) return st;
+    if (!diagonal) flush();
+    std::vector<LOp>& dst = diagonal ? run_ops : ops;
+    if (G.param >= 0) (diagonal ? run_grads : ops).push_back(go);
     for (int j = 0; j < L.nops; j++) {
       L.op[j].gate = gi;
       if (j == 0) {
         L.op[j].fr = L.zr;
         L.op[j].fi = L.zi;
       }
-      ops.push_back(L.op[j]);
+      dst.push_back(L.op[j]);
     }
     double nr = zr * L.zr - zi * L.zi, ni = zr * L.zi + zi * L.zr;
     zr = nr;
@@ -306,12 +411,14 @@ static lq_status build_sweep(int n, const lq_gate* gates, int ng, const double* 
       sc.mode = 1;
       sc.a = mag;
       sc.fr = 1.0 / mag;
-      ops.push_back(sc);
+      dst.push_back(sc);
       zr /= mag;
       zi /= mag;
     }
   }
+  flush();
   ScheduleOptions sopt;
+  sopt.k = tile_bits;
   st = schedule_ops(n, ops.data(), ops.size(), zr, zi, sopt, S);
   if (st) return st;
   // A gradient op sees the states divided by the deferred scalar accumulated
@@ -353,9 +460,10 @@ lq_status lq_adjoint_plan(int n, const lq_gate* gates, int ng, const double* par
   std::vector<double> factor;
   std::vector<int> slot_param;
   Schedule S;
-  st = build_sweep(n, gates, ng, params, ops, factor, slot_param, S);
+  st = build_sweep(n, gates, ng, params, ops, factor, slot_param, S, sweep_tile_bits(n));
   if (st) return st;
   double fl = fwd.dp_flops;
+  const double N = std::ldexp(1.0, n);
   int rev = 0;
   for (int p = 0; p < S.npasses; p++) {
     int nops = S.passes[p].h.nops;
@@ -364,7 +472,24 @@ lq_status lq_adjoint_plan(int n, const lq_gate* gates, int ng, const double* par
       nops--;
     if (nops == 0) continue;
     rev++;
-    for (const LOp& l : S.pass_ops[p]) fl += (l.type == OP_GRAD ? 1.0 : 2.0) * op_flops(l, n);
+    const std::vector<LOp>& L = S.pass_ops[p];
+    for (std::size_t i = 0; i < L.size(); i++) {
+      const LOp& l = L[i];
+      if (l.type == OP_GRAD && l.x == 0 && (l.mode & 3) == 0 && S.passes[p].h.k <= 11) {
+        // a run of diagonal generators: q_s (3 flops) and the Walsh-Hadamard
+        // transform over a thread's 8 amplitudes (3 adds) per amplitude
+        while (i + 1 < L.size() && L[i + 1].type == OP_GRAD && L[i + 1].x == 0 &&
+               (L[i + 1].mode & 3) == 0)
+          i++;
+        fl += 6.0 * N;
+      } else if (l.type == OP_GRAD) {
+        fl += op_flops(l, n);
+      } else if (l.type == OP_LPHASE && !(l.mode & LP_TABLE)) {
+        fl += op_flops(l, n) + 6.0 * N;   // one phase per amplitude, two multiplies
+      } else {
+        fl += 2.0 * op_flops(l, n);
+      }
+    }
   }
   const int chunks = nt > 0 ? (nt + EXP_MAX_TERMS - 1) / EXP_MAX_TERMS : 0;
   // init, forward passes, <H> (2 per chunk), H psi (1 per chunk), reverse
@@ -401,9 +526,7 @@ lq_status lq_adjoint_grad(int n, const lq_gate* gates, int ng, const double* par
     return fail(LQ_ERR_OOM, "workspace too small: %zu < %zu", ws_bytes, need);
   cudaStream_t s = (cudaStream_t)stream;
   const std::size_t sb = sizeof(double2) << n;
-  ScheduleOptions opt;
-  const int k = opt.k < n ? opt.k : n;
-  const int grid = pass2_grid(n, k);
+  const int grid = pass2_grid(n, n < 10 ? n : 10);   // stride of the partial sums
 
   // workspace layout
   char* p = (char*)workspace;
@@ -438,7 +561,7 @@ lq_status lq_adjoint_grad(int n, const lq_gate* gates, int ng, const double* par
   std::vector<double> factor;
   std::vector<int> slot_param;
   Schedule S;
-  st = build_sweep(n, gates, ng, params, ops, factor, slot_param, S);
+  st = build_sweep(n, gates, ng, params, ops, factor, slot_param, S, sweep_tile_bits(n));
   if (st) return st;
   const int nslots = (int)factor.size();
   // slots grouped by parameter, in slot order

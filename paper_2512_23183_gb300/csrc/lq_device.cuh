@@ -406,13 +406,16 @@ struct PassTables {
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
 // are `base`; dtab: the dyadic phase tables; tabs: the pass's per-CTA tables
 // (pass_kernel), or nullptr; pt: the circuit's patch (batched launches: the
-// patched gate's factor of a merged one-bit phase op), or nullptr.
+// patched gate's factor of a merged one-bit phase op), or nullptr; sm2: a
+// second tile that a per-tile-mode OP_LPHASE multiplies by the same phases
+// (two-state passes), or nullptr.
 template <int BLOCK>
 __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, const Op& op,
                                          const double* __restrict__ coef, uint64_t base,
                                          const double2* __restrict__ dtab,
                                          const PassTables* tabs = nullptr,
-                                         const Patch* pt = nullptr) {
+                                         const Patch* pt = nullptr,
+                                         double2* __restrict__ sm2 = nullptr) {
   const uint32_t tid = threadIdx.x;
   // per-tile tables of OP_DPHASE (2 x 128 sums) or OP_LPHASE (2 x 128
   // phases); one op at a time uses it
@@ -812,6 +815,7 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
           w = cmul(w, w1.x, w1.y);
         }
         sm[s] = cmul(sm[s], w.x, w.y);
+        if (sm2) sm2[s] = cmul(sm2[s], w.x, w.y);
       }
       break;
     }

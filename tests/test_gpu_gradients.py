@@ -61,6 +61,45 @@ def test_adjoint_general_gates_vs_finite_differences(lq, n, seed):
     np.testing.assert_allclose(g, fd, rtol=0, atol=1e-6)
 
 
+def diagonal_run_circuit(n, rng, layers=3):
+    """RY layers separated by long runs of diagonal gates (RZ, P, CP, CRZ,
+    RZZ with parameters, some shared; S, T, CZ fixed): the reverse sweep
+    takes each run's gradients together."""
+    gates, p = [], 0
+    for _ in range(layers):
+        for q in range(n):
+            gates.append(W.G("RY", q, param=p)); p += 1
+        for q in range(n):
+            gates.append(W.G("RZ", q, param=p)); p += 1
+            a, b = q, (q + 1 + int(rng.integers(n - 1))) % n
+            kind = ["P", "CP", "CRZ", "RZZ", "S", "T", "CZ"][int(rng.integers(7))]
+            if kind == "P":
+                gates.append(W.G("P", a, param=int(rng.integers(p))))   # shared parameter
+            elif kind in ("CP", "CRZ", "RZZ"):
+                gates.append(W.G(kind, a, b, param=p)); p += 1
+            else:
+                gates.append(W.G(kind, *((a, b) if kind == "CZ" else (a,))))
+        for q in range(n - 1):
+            gates.append(W.G("CNOT", q, q + 1))
+    return gates, p
+
+
+@pytest.mark.parametrize("n,seed", [(9, 5), (13, 6), (16, 7)])
+def test_adjoint_diagonal_runs(lq, n, seed):
+    rng = np.random.default_rng(seed)
+    gates, P = diagonal_run_circuit(n, rng, layers=3 if n < 16 else 2)
+    th = rng.uniform(-np.pi, np.pi, P)
+    terms = W.random_pauli_sum(n, 20, rng, kmin=1, kmax=3)
+    e_w, g_w = oracle.param_shift(n, gates, th, terms, general=True)
+    e, g = lq.adjoint_grad(n, gates, th, terms)
+    assert abs(e - e_w) <= RTOL * max(1, abs(e_w))
+    np.testing.assert_allclose(g, g_w, rtol=0, atol=RTOL * max(1.0, np.abs(g_w).max()))
+    if n == 13:
+        idx = rng.choice(P, 12, replace=False)
+        fd = oracle.finite_diff(n, gates, th, terms, h=1e-4, which=idx)
+        np.testing.assert_allclose(g[idx], fd, rtol=0, atol=1e-6)
+
+
 def _appd_rows():
     rows = []
     with open(os.path.join(os.path.dirname(__file__), "golden", "appD_psr_table.txt")) as f:
