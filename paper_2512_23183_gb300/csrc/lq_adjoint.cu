@@ -43,6 +43,65 @@ static constexpr int kPassBlock = 256;
 
 // ------------------------------------------------------- two-state passes
 
+// Warp sums of gradient terms, four at a time: each lane holds its partial
+// value of up to four consecutive terms; a transposing butterfly (lanes
+// exchange the terms they do not keep) leaves lane t < 4 with term t's warp
+// sum after 6 adds and 6 double shuffles, against 20 and 20 for four plain
+// shuffle reductions.  gacc[term][warp] collects the sums over the tiles.
+struct GradBatch {
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+  int n = 0, first = 0;
+};
+
+__device__ __forceinline__ void grad_flush(GradBatch& b, double* gacc, int nw, int warp) {
+  if (b.n == 0) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const bool o1 = lane & 1, o2 = lane & 2;
+  // lanes with bit 0 set keep terms 1 and 3, the others 0 and 2
+  const double k0 = (o1 ? b.v1 : b.v0) + __shfl_xor_sync(0xffffffffu, o1 ? b.v0 : b.v1, 1);
+  const double k1 = (o1 ? b.v3 : b.v2) + __shfl_xor_sync(0xffffffffu, o1 ? b.v2 : b.v3, 1);
+  // lanes with bit 1 set keep terms 2|3, the others 0|1: lane holds term lane & 3
+  double kept = (o2 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, o2 ? k0 : k1, 2);
+  kept += __shfl_xor_sync(0xffffffffu, kept, 4);
+  kept += __shfl_xor_sync(0xffffffffu, kept, 8);
+  kept += __shfl_xor_sync(0xffffffffu, kept, 16);
+  if (lane < (uint32_t)b.n) gacc[(b.first + (int)lane) * nw + warp] += kept;
+  b = GradBatch();
+}
+
+// Add this thread's value v of gradient term gl (terms arrive in order).
+__device__ __forceinline__ void grad_push(GradBatch& b, double v, int gl, double* gacc, int nw,
+                                          int warp) {
+  if (b.n == 0) b.first = gl;
+  switch (b.n) {
+    case 0: b.v0 = v; break;
+    case 1: b.v1 = v; break;
+    case 2: b.v2 = v; break;
+    default: b.v3 = v; break;
+  }
+  if (++b.n == 4) grad_flush(b, gacc, nw, warp);
+}
+
+// A gradient op and the op after it fuse (grad_rot1_pairs) when both act on
+// the same single tile bit without conditions, the generator's Z part lies
+// on that bit, and the rotation is in tangent or cotangent form with phases
+// of the parity opposite to the generator's.
+__device__ __forceinline__ bool fusable_grad_rot(const Op& g, const Op& r) {
+  if (r.type != OP_PAULI || g.x_loc == 0 || g.x_loc != r.x_loc || (g.x_loc & (g.x_loc - 1)) != 0)
+    return false;
+  if (g.cm_loc | r.cm_loc | g.cm_glob | r.cm_glob) return false;
+  if ((g.z_loc & ~g.x_loc) | (r.z_loc & ~r.x_loc)) return false;
+  const int pm = r.mode & 3;
+  if (pm != PM_TAN && pm != PM_COT) return false;
+  // rotation phase parity (r.mode >> 2) against the generator's (i^k0)
+  return ((r.mode >> 2) & 1) != (g.mode & 1);
+}
+
+// Op o only reads the tiles: a gradient op not fused with the op after it.
+__device__ __forceinline__ bool grad_reads_only(const Op* ops, int o, int nops) {
+  return ops[o].type == OP_GRAD && !(o + 1 < nops && fusable_grad_rot(ops[o], ops[o + 1]));
+}
+
 // Gradient terms of a run of diagonal generators G_t (Z strings z_t under
 // conditions cm_t/cv_t; x = 0, no factor i) on the two tiles A = psi,
 // B = lambda: Im <lambda|G_t|psi> = sum_s G_t(s) q_s with
@@ -56,12 +115,12 @@ static constexpr int kPassBlock = 256;
 // cv expands as prod_b (1 + (-1)^(s_b + cv_b)) / 2 over its bits:
 //   sum_s [cond(s)] (-1)^popcount(s & z) q_s
 //     = 2^-|cm| sum_{S subset of cm} (-1)^popcount(cv & S) W(z ^ S).
-// Each term's CTA sum is added (by lane 0 of each warp) to acc[t * stride].
+// Each term's value goes to the warp's gradient batch as term gl + t.
 template <int BLOCK>
 __device__ __forceinline__ void diag_grad_terms(const double2* __restrict__ A,
                                                 const double2* __restrict__ B, uint32_t T,
                                                 const Op* ops, int nterms, uint64_t base,
-                                                double* acc, int stride) {
+                                                GradBatch& gb, int gl, double* gacc, int nw) {
   constexpr int LB = BLOCK == 1024 ? 10 : BLOCK == 512 ? 9 : BLOCK == 256 ? 8 : 7;
   static_assert((1 << LB) == BLOCK, "BLOCK must be a power of two in 128..1024");
   const uint32_t tid = threadIdx.x;
@@ -104,8 +163,51 @@ __device__ __forceinline__ void diag_grad_terms(const double2* __restrict__ A,
       v = ldexp(v, -__popc(cm));
       if (__popcll(base & d.z_glob) & 1) v = -v;
     }
-    for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
-    if ((tid & 31) == 0) acc[t * stride] += v;
+    grad_push(gb, v, gl + t, gacc, nw, (int)(tid >> 5));
+  }
+}
+
+// A one-bit rotation's gradient op fused with the rotation that follows it
+// in the sweep (U_k^dag of the same gate, or any one-bit rotation on the same
+// bit without conditions): one pass over the amplitude pairs (s0, s1 = s0|x)
+// adds the gradient terms Im(conj(lambda_s0) i^gA psi_s1) and
+// Im(conj(lambda_s1) i^gB psi_s0) and rotates both states' pairs.  For RY
+// the gradient phases are odd and the rotation's even, for RX the reverse
+// (ODD = rotation phases odd); the gradient signs (gA, gB & 2) are applied
+// to the sums afterwards.  Same FP64 work as the separate ops, half the
+// shared-memory reads and one barrier instead of two.
+template <int BLOCK, int FORM, bool ODD>
+__device__ __forceinline__ void grad_rot1_pairs(double2* __restrict__ A, double2* __restrict__ B,
+                                                uint32_t T, uint32_t x, double a, double cA,
+                                                double cB, uint32_t sA, uint32_t sB,
+                                                double& accA, double& accB) {
+  const uint32_t tid = threadIdx.x;
+  const int h = 31 - __clz(x);
+  // acc += Im(conj(l) i^g v) up to the sign of g
+  auto term = [&](double& acc, double2 l, double2 v) {
+    acc = ODD ? fma(l.x, v.y, fma(-l.y, v.x, acc)) : fma(l.x, v.x, fma(l.y, v.y, acc));
+  };
+  auto rot = [&](double2 u0, double2 u1, double2& o0, double2& o1) {
+    if (FORM == ROT_TAN) {
+      o0 = rot_fma<ODD>(cA, u1, u0);
+      o1 = rot_fma<ODD>(cB, u0, u1);
+    } else {
+      o0 = rot_cot<ODD>(a, u0, u1, sA);
+      o1 = rot_cot<ODD>(a, u1, u0, sB);
+    }
+  };
+  for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
+    const uint32_t s0 = insert0(j, h), s1 = s0 | x;
+    const double2 p0 = A[s0], p1 = A[s1], l0 = B[s0], l1 = B[s1];
+    term(accA, l0, p1);
+    term(accB, l1, p0);
+    double2 o0, o1;
+    rot(p0, p1, o0, o1);
+    A[s0] = o0;
+    A[s1] = o1;
+    rot(l0, l1, o0, o1);
+    B[s0] = o0;
+    B[s1] = o1;
   }
 }
 
@@ -148,6 +250,7 @@ __global__ void __launch_bounds__(BLOCK, 3) pass2_kernel(const __grid_constant__
     }
     __syncthreads();
     int gl = 0;
+    GradBatch gb;
     for (int o = 0; o < nops; o++) {
       const Op& op = P.ops[o];
       if (op.type == OP_GRAD && op.x_loc == 0 && (op.mode & 3) == 0 && T <= 8 * BLOCK) {
@@ -157,10 +260,37 @@ __global__ void __launch_bounds__(BLOCK, 3) pass2_kernel(const __grid_constant__
         while (e < nops && P.ops[e].type == OP_GRAD && P.ops[e].x_loc == 0 &&
                (P.ops[e].mode & 3) == 0)
           e++;
-        diag_grad_terms<BLOCK>(A, B, T, P.ops + o, e - o, base, gacc + gl * NW + warp, NW);
+        diag_grad_terms<BLOCK>(A, B, T, P.ops + o, e - o, base, gb, gl, gacc, NW);
         gl += e - o;
         o = e - 1;
-        if (e < nops && P.ops[e].type != OP_GRAD) __syncthreads();
+        // the next op may overwrite what this one read
+        if (e < nops && !grad_reads_only(P.ops, e, nops)) __syncthreads();
+      } else if (op.type == OP_GRAD && o + 1 < nops && fusable_grad_rot(op, P.ops[o + 1])) {
+        const Op& r = P.ops[o + 1];
+        double accA = 0.0, accB = 0.0;
+        const int zsg = __popcll(base & op.z_glob) & 1, zsr = __popcll(base & r.z_glob) & 1;
+        const int k0 = op.mode & 3;
+        const int gA = (k0 + 2 * ((op.z_loc != 0) + zsg)) & 3, gB = (k0 + 2 * zsg) & 3;
+        const int rk0 = r.mode >> 2;
+        const int kA = (rk0 + 2 * ((r.z_loc != 0) + zsr)) & 3, kB = (rk0 + 2 * zsr) & 3;
+        const double a = r.a, cA = (kA & 2) ? -a : a, cB = (kB & 2) ? -a : a;
+        const uint32_t sA = (uint32_t)(kA & 2) << 30, sB = (uint32_t)(kB & 2) << 30;
+        const bool odd = kA & 1;
+        if ((r.mode & 3) == PM_TAN) {
+          if (odd)
+            grad_rot1_pairs<BLOCK, ROT_TAN, true>(A, B, T, r.x_loc, a, cA, cB, sA, sB, accA, accB);
+          else
+            grad_rot1_pairs<BLOCK, ROT_TAN, false>(A, B, T, r.x_loc, a, cA, cB, sA, sB, accA, accB);
+        } else {
+          if (odd)
+            grad_rot1_pairs<BLOCK, ROT_COT, true>(A, B, T, r.x_loc, a, cA, cB, sA, sB, accA, accB);
+          else
+            grad_rot1_pairs<BLOCK, ROT_COT, false>(A, B, T, r.x_loc, a, cA, cB, sA, sB, accA, accB);
+        }
+        grad_push(gb, ((gA & 2) ? -accA : accA) + ((gB & 2) ? -accB : accB), gl, gacc, NW, warp);
+        gl++;
+        o++;
+        __syncthreads();
       } else if (op.type == OP_GRAD) {
         double acc = 0.0;
         if ((base & op.cm_glob) == op.cv_glob) {
@@ -175,11 +305,10 @@ __global__ void __launch_bounds__(BLOCK, 3) pass2_kernel(const __grid_constant__
             acc = fma(l.x, v.y, fma(-l.y, v.x, acc));
           }
         }
-        for (int sh = 16; sh > 0; sh >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sh);
-        if ((threadIdx.x & 31) == 0) gacc[gl * NW + warp] += acc;
+        grad_push(gb, acc, gl, gacc, NW, warp);
         gl++;
         // the next op may overwrite what this one read
-        if (o + 1 < nops && P.ops[o + 1].type != OP_GRAD) __syncthreads();
+        if (o + 1 < nops && !grad_reads_only(P.ops, o + 1, nops)) __syncthreads();
       } else if (op.type == OP_LPHASE && !(op.mode & LP_TABLE)) {
         // the same per-tile phase tables serve both states
         apply_op<BLOCK>(A, T, op, P.coef, base, (const double2*)P.h.dtab, nullptr, nullptr, B);
@@ -190,6 +319,7 @@ __global__ void __launch_bounds__(BLOCK, 3) pass2_kernel(const __grid_constant__
         __syncthreads();
       }
     }
+    grad_flush(gb, gacc, NW, warp);
     for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
       const uint64_t g = base | hioff[s >> m] | (s & lowmask);
       psi[g] = A[s];
@@ -419,6 +549,9 @@ static lq_status build_sweep(int n, const lq_gate* gates, int ng, const double* 
   flush();
   ScheduleOptions sopt;
   sopt.k = tile_bits;
+  // 56 gradient sums (8 warps, 3.5 KiB) keep three CTAs with two 32 KiB
+  // tiles resident per SM
+  sopt.max_grads = 56;
   st = schedule_ops(n, ops.data(), ops.size(), zr, zi, sopt, S);
   if (st) return st;
   // A gradient op sees the states divided by the deferred scalar accumulated

@@ -564,20 +564,22 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
   while (!pending.empty()) {
     Built B;
     B.tile = low;
-    int coefs = 0;
+    int coefs = 0, grads = 0;
     std::vector<int> skipped;
     uint64_t blocked_mix = 0, blocked_all = 0;
     for (int idx : pending) {
       const LOp& o = ops[idx];
       uint64_t mx = o.mix(), dg = o.diag();
       bool commutes = !(mx & blocked_all) && !(dg & blocked_mix);
-      bool room = (int)B.idx.size() < MAX_OPS - 1 && coefs + o.ncoef <= MAX_COEF;
+      bool room = (int)B.idx.size() < MAX_OPS - 1 && coefs + o.ncoef <= MAX_COEF &&
+                  (o.type != OP_GRAD || grads < opt.max_grads);
       if (commutes && room) {
         uint64_t t = B.tile | mx;
         if (popc64(t) <= k) {
           B.tile = t;
           B.idx.push_back(idx);
           coefs += o.ncoef;
+          grads += o.type == OP_GRAD;
           continue;
         }
       }

@@ -210,6 +210,8 @@ struct ScheduleOptions {
   int m = 5;                 // contiguous low bits always in the tile
   bool force_scale = false;  // always end with a (final) OP_SCALE
   bool merge_params = true;  // merge one-bit phases of parametrised gates too
+  int max_grads = 1 << 30;   // OP_GRAD ops per pass (two-state passes keep a
+                             // shared-memory sum per gradient op and warp)
   bool lphase_table = false; // mark one OP_LPHASE per pass for a per-CTA table,
                              // and OP_DPHASE ops for per-CTA partial-sum tables
                              // (schedules run by pass_kernel only)
