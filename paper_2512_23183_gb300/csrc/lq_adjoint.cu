@@ -549,9 +549,9 @@ static lq_status build_sweep(int n, const lq_gate* gates, int ng, const double* 
   flush();
   ScheduleOptions sopt;
   sopt.k = tile_bits;
-  // 56 gradient sums (8 warps, 3.5 KiB) keep three CTAs with two 32 KiB
-  // tiles resident per SM
-  sopt.max_grads = 56;
+  // with two 32 KiB tiles, 56 gradient sums (8 warps, 3.5 KiB) keep three
+  // CTAs resident per SM; smaller tiles leave room for a pass's every op
+  sopt.max_grads = tile_bits >= 11 ? 56 : MAX_OPS;
   st = schedule_ops(n, ops.data(), ops.size(), zr, zi, sopt, S);
   if (st) return st;
   // A gradient op sees the states divided by the deferred scalar accumulated

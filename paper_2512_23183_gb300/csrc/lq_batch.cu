@@ -15,6 +15,7 @@
 // state in the workspace.  Circuits of one problem share one op program
 // lowered at the base angles; a circuit differs only in the coefficients of
 // its shifted gate and in the deferred scalar (a Patch).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -476,15 +477,44 @@ static std::size_t batch_bytes(const BatchPlan& B, int grid) {
 //
 // A batch run is four stream operations: upload the program image, reset the
 // two counters, the persistent kernel, download the results.  They are
-// captured once per layout (workspace address, section sizes, grid) into a
-// CUDA graph on an internal stream of the device and replayed; a replay
+// captured once per layout (workspace allocation, section sizes, grid) into
+// a CUDA graph on an internal stream of the device and replayed; a replay
 // only rewrites the pinned staging image (new angles give new coefficients,
 // never a new layout).  Events order the replay after the caller's stream
 // work and the caller's stream after the replay.
+//
+// A graph's copy and memset nodes belong to the allocation they were
+// captured on, not just to its address: after the caller frees a workspace,
+// a new allocation can come back at the same address (a caching allocator
+// returning memory to the driver and taking it again does this), and
+// replaying the old graph on it faulted or left the upload in the freed
+// memory.  So an entry also records the allocation's process-wide buffer id
+// and is used only while the workspace is that same allocation; when the id
+// cannot be read, the graph is not kept.
+
+// Process-wide unique id of the device allocation holding p, 0 if unknown.
+static unsigned long long allocation_id(const void* p) {
+  using GetAttr = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+  static GetAttr fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    (void)cudaGetLastError();
+    return reinterpret_cast<GetAttr>(f);
+  }();
+  if (!fn) return 0;
+  unsigned long long id = 0;
+  if (fn(&id, CU_POINTER_ATTRIBUTE_BUFFER_ID, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 struct GraphEntry {
   int device = -1;
   void* ws = nullptr;
+  unsigned long long ws_id = 0;   // buffer id of the workspace allocation
   std::vector<std::size_t> key;
   cudaGraphExec_t exec = nullptr;
   char* h_image = nullptr;      // pinned
@@ -577,9 +607,21 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
     LQ_CUDA(cudaEventCreateWithFlags(&g_ev_out[dev], cudaEventDisableTiming));
   }
   cudaStream_t gs = g_graph_stream[dev];
+  const unsigned long long ws_id = allocation_id(workspace);
+  // entries on a freed workspace (the address now names another allocation),
+  // or left by a run whose allocation was unknown
+  for (std::size_t i = 0; i < g_graphs.size();) {
+    if (g_graphs[i].device == dev && g_graphs[i].ws == workspace &&
+        (g_graphs[i].ws_id != ws_id || ws_id == 0)) {
+      drop_entry(g_graphs[i]);
+      g_graphs.erase(g_graphs.begin() + (long)i);
+    } else {
+      i++;
+    }
+  }
   GraphEntry* E = nullptr;
   for (auto& e : g_graphs)
-    if (e.device == dev && e.ws == workspace && e.key == key) E = &e;
+    if (e.device == dev && e.ws == workspace && e.ws_id == ws_id && e.key == key) E = &e;
   if (!E) {
     // capture a new graph for this layout (evict the least recently used)
     if (g_graphs.size() >= kMaxGraphs) {
@@ -592,6 +634,7 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
     GraphEntry ne;
     ne.device = dev;
     ne.ws = workspace;
+    ne.ws_id = ws_id;
     ne.key = key;
     ne.image = image;
     ne.nout = (std::size_t)B.nout;
@@ -630,6 +673,10 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
   LQ_CUDA(cudaStreamWaitEvent(s, g_ev_out[dev], 0));
   LQ_CUDA(cudaStreamSynchronize(gs));
   out.assign(E->h_out, E->h_out + B.nout);
+  if (ws_id == 0) {   // allocation unknown: do not keep the graph
+    drop_entry(*E);
+    g_graphs.erase(g_graphs.begin() + (E - g_graphs.data()));
+  }
   return LQ_OK;
 }
 

@@ -403,66 +403,6 @@ struct PassTables {
   unsigned long long* dfe;           // full mode: this tile's deferred sums
 };
 
-// A full-mode OP_DPHASE conditioned on one tile bit c being set and an OP_H
-// on bit c, adjacent in either order, run as one pass over the pairs
-// (s0, s1 = s0 | 2^c) (the gate-form QFT's H / controlled-phase runs): the
-// phase of s1 is the op's table entry j, j the pair index, so
-// phase-then-H gives (A + wB, A - wB) and H-then-phase (A + B, w (A - B)).
-// Same FP64 work as the two ops, one tile sweep and one barrier fewer.
-__device__ __forceinline__ bool fusable_dphase_h(const Op& d, const Op& h,
-                                                 const PassTables* tabs) {
-  return d.type == OP_DPHASE && (d.mode & DP_TABLE) && (d.mode & DP_FULL) && tabs &&
-         tabs->dpt && tabs->dfull && d.cm_glob == 0 && d.cm_loc != 0 &&
-         (d.cm_loc & (d.cm_loc - 1)) == 0 && d.cv_loc == d.cm_loc && h.type == OP_H &&
-         h.cm_loc == 0 && h.cm_glob == 0 && (1u << h.b0) == d.cm_loc;
-}
-
-template <int BLOCK, bool PHASE_FIRST>
-__device__ __forceinline__ void dphase_h_pairs(double2* __restrict__ sm, uint32_t T, const Op& d,
-                                               uint64_t base, const PassTables* tabs) {
-  const uint32_t tid = threadIdx.x;
-  if (!(d.mode & DP_PRE)) {   // this tile's constant part, applied at the store
-    const unsigned long long e0 = dphase_tile_sum(tabs->dpt + d.z_loc, (int)d.b1, base);
-    if (tid == 0) tabs->dfe[d.b0] = e0;
-  }
-  const double2* __restrict__ F = tabs->dfull + d.z_glob;
-  const uint32_t xb = d.cm_loc;
-  const int c = __ffs(xb) - 1;
-  const uint32_t cnt = T >> 1;
-  auto out = [&](double2 A, double2 B, double2 w, double2& o0, double2& o1) {
-    if (PHASE_FIRST) {
-      const double2 t = cmul(B, w.x, w.y);
-      o0 = make_double2(A.x + t.x, A.y + t.y);
-      o1 = make_double2(A.x - t.x, A.y - t.y);
-    } else {
-      o0 = make_double2(A.x + B.x, A.y + B.y);
-      o1 = cmul(make_double2(A.x - B.x, A.y - B.y), w.x, w.y);
-    }
-  };
-  if ((cnt & (2 * BLOCK - 1)) == 0) {
-    for (uint32_t j = tid; j < cnt; j += 2 * BLOCK) {
-      const uint32_t p0 = insert0(j, c), q0 = insert0(j + BLOCK, c);
-      const double2 A = sm[p0], B = sm[p0 | xb], C = sm[q0], D = sm[q0 | xb];
-      const double2 w0 = F[j], w1 = F[j + BLOCK];
-      double2 o0, o1, o2, o3;
-      out(A, B, w0, o0, o1);
-      out(C, D, w1, o2, o3);
-      sm[p0] = o0;
-      sm[p0 | xb] = o1;
-      sm[q0] = o2;
-      sm[q0 | xb] = o3;
-    }
-  } else {
-    for (uint32_t j = tid; j < cnt; j += BLOCK) {
-      const uint32_t s0 = insert0(j, c);
-      double2 o0, o1;
-      out(sm[s0], sm[s0 | xb], F[j], o0, o1);
-      sm[s0] = o0;
-      sm[s0 | xb] = o1;
-    }
-  }
-}
-
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
 // are `base`; dtab: the dyadic phase tables; tabs: the pass's per-CTA tables
 // (pass_kernel), or nullptr; pt: the circuit's patch (batched launches: the

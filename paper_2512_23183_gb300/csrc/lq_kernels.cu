@@ -208,15 +208,7 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
       __syncthreads();
     }
     for (int o = 0; o < nops; o++) {
-      if (o + 1 < nops && fusable_dphase_h(P.ops[o], P.ops[o + 1], &tabs)) {
-        dphase_h_pairs<BLOCK, true>(sm, T, P.ops[o], base, &tabs);
-        o++;
-      } else if (o + 1 < nops && fusable_dphase_h(P.ops[o + 1], P.ops[o], &tabs)) {
-        dphase_h_pairs<BLOCK, false>(sm, T, P.ops[o + 1], base, &tabs);
-        o++;
-      } else {
-        apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab, &tabs);
-      }
+      apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab, &tabs);
       __syncthreads();
     }
     if (post) {

@@ -63,3 +63,31 @@ def test_batched_psr_n16_ring(lq):
     e, g = lq.param_shift_grad(n, gates, th, terms, method=lq.PSR_BATCHED)
     assert abs(e - e_w) <= RTOL * max(1, abs(e_w))
     np.testing.assert_allclose(g, g_w, rtol=0, atol=RTOL * max(1.0, np.abs(g_w).max()))
+
+
+def test_batched_after_workspace_reallocation(lq):
+    """A replayed launch must follow its workspace: free the workspace and
+    hand the memory back to the driver, allocate again (the address usually
+    repeats) and the batched gradient still matches the oracle."""
+    import torch
+
+    n, depth = 10, 4
+    gates, P = W.hea(n, depth, "ladder")
+    terms = W.heisenberg(n)
+    need = lq.load().lq_param_shift_workspace_size(n, P, len(terms), lq.PSR_BATCHED)
+    addrs = []
+    for rep in range(4):
+        th = W.angles(P, 60 + rep)
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        addrs.append(ws.data_ptr())
+        e, g = lq.param_shift_grad(n, gates, th, terms, method=lq.PSR_BATCHED, workspace=ws)
+        e_w, g_w = oracle.param_shift(n, gates, th, terms)
+        assert abs(e - e_w) <= RTOL * max(1, abs(e_w)), rep
+        np.testing.assert_allclose(g, g_w, rtol=0, atol=RTOL * max(1.0, np.abs(g_w).max()))
+        del ws
+        # other allocations come and go, then the cache is returned to the driver
+        big = torch.empty(1 << 28, dtype=torch.uint8, device="cuda")
+        del big
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    assert len(addrs) == 4

@@ -135,7 +135,8 @@ def test_adjoint_n24_config_sampled(lq):
         return lq.expval_pauli_sum(t, n, terms, workspace=ws)
 
     assert _close(e, energy(th))
-    for i in (0, 191, 479):
+    # RY and RZ gates of first, middle and last layers (local and CTA bits)
+    for i in (0, 191, 250, 325, 479):
         p = th.copy()
         p[i] += np.pi / 2
         ep = energy(p)
