@@ -340,8 +340,10 @@ __global__ void __launch_bounds__(BLOCK, 3) pass2_kernel(const __grid_constant__
 }
 
 // Tile bits of the reverse sweep: two 32 KiB tiles per CTA (3 CTAs per SM)
-// measured 11% faster than 2^10-amplitude tiles at n = 24 (fewer passes).
-static int sweep_tile_bits(int n) { return n < 11 ? n : 11; }
+// measured 11% faster than 2^10-amplitude tiles at n = 24 (fewer passes);
+// below n = 20 they would leave SMs idle (2^(n-11) < 2 x 152 tiles), so
+// smaller states keep 2^10-amplitude tiles.
+static int sweep_tile_bits(int n) { return n >= 20 ? 11 : n < 10 ? n : 10; }
 
 // Largest grid of a two-state pass (the stride of the partial sums): tiles
 // of 2^k amplitudes, up to 6 CTAs per SM; passes with wider tiles launch
@@ -370,14 +372,20 @@ cudaError_t launch_pass2(const PassParams& P, double2* psi, double2* lam, double
   int ngrad = 0;
   for (int o = 0; o < P.h.nops; o++) ngrad += P.ops[o].type == OP_GRAD;
   const size_t smem = 2 * (sizeof(double2) << P.h.k) + sizeof(double) * NW * ngrad;
-  // one wave of resident CTAs (registers and shared memory)
-  int per_sm = 0;
-  cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, pass2_kernel<kPassBlock>, kPassBlock, smem);
-  if (oe != cudaSuccess) return oe;
-  per_sm = per_sm < 1 ? 1 : per_sm;
-  uint64_t g = (uint64_t)sm_count() * per_sm;
-  if (g > P.h.ntiles) g = P.h.ntiles;
+  // one wave of resident CTAs (registers and shared memory); with tiles of
+  // at most 2^11 amplitudes two CTAs per SM always fit, so fewer tiles than
+  // that need no occupancy query (it costs microseconds per launch, which
+  // small states feel)
+  uint64_t g = P.h.ntiles;
+  if (P.h.k > 11 || g > 2 * (uint64_t)sm_count()) {
+    int per_sm = 0;
+    cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, pass2_kernel<kPassBlock>, kPassBlock, smem);
+    if (oe != cudaSuccess) return oe;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    g = (uint64_t)sm_count() * per_sm;
+    if (g > P.h.ntiles) g = P.h.ntiles;
+  }
   const int pgrid = (int)g < grid ? (int)g : grid;
   if (P.h.flags & PF_DYADIC) {
     cudaError_t e;
