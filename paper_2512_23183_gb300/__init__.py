@@ -202,28 +202,70 @@ def version():
 
 # ------------------------------------------------------------- marshalling
 
+# numpy layout of lq_gate (the struct is filled column-wise, then viewed by ctypes)
+_GATE_DTYPE = np.dtype([("kind", "<i4"), ("qubits", "<i4", (3,)), ("param", "<i4"),
+                        ("reserved", "<i4"), ("angle", "<f8"), ("mat", "<f8", (32,))])
+
+
+_GATE_CACHE = {}
+
+
 def pack_gates(gates):
-    arr = (LqGate * max(len(gates), 1))()
-    for i, g in enumerate(gates):
-        G = arr[i]
-        G.kind = KINDS[g.name]
-        q = list(g.qubits) + [-1] * (3 - len(g.qubits))
-        for j in range(3):
-            G.qubits[j] = q[j]
-        G.param = g.param
-        G.angle = g.angle
-        if g.mat is not None:
-            m = np.ascontiguousarray(np.asarray(g.mat, np.complex128).reshape(-1)).view(np.float64)
-            for j, v in enumerate(m):
-                G.mat[j] = float(v)
+    """The gate list as a ctypes lq_gate array (sharing one numpy buffer); the
+    packing of a given gate sequence is kept (gates carry no parameter
+    values, so an optimisation loop passes the same sequence every call)."""
+    try:
+        key = tuple(gates)
+        hash(key)
+    except TypeError:   # a gate with a matrix (numpy array) is not hashable
+        key = None
+    if key is not None:
+        hit = _GATE_CACHE.get(key)
+        if hit is not None:
+            return hit
+    arr = _pack_gates(gates)
+    if key is not None:
+        if len(_GATE_CACHE) > 64:
+            _GATE_CACHE.clear()
+        _GATE_CACHE[key] = arr
     return arr
 
 
+def _pack_gates(gates):
+    m = len(gates)
+    a = np.zeros(max(m, 1), _GATE_DTYPE)
+    if m:
+        a["kind"][:m] = [KINDS[g.name] for g in gates]
+        a["qubits"][:m] = [tuple(g.qubits) + (-1,) * (3 - len(g.qubits)) for g in gates]
+        a["param"][:m] = [g.param for g in gates]
+        a["angle"][:m] = [g.angle for g in gates]
+        for i, g in enumerate(gates):
+            if g.mat is not None:
+                v = np.ascontiguousarray(np.asarray(g.mat, np.complex128).reshape(-1)).view(np.float64)
+                a["mat"][i, : v.size] = v
+    return (LqGate * a.size).from_buffer(a)
+
+
+_TERM_CACHE = {}
+
+
 def pack_terms(terms, n):
+    """The Pauli sum as a ctypes lq_pauli_term array; the packing of a given
+    (terms, n) is kept (a VQE loop passes the same Hamiltonian every call)."""
+    try:
+        key = (n, tuple((float(c), str(s)) for c, s in terms))
+    except (TypeError, ValueError):
+        key = None
+    if key is not None and key in _TERM_CACHE:
+        return _TERM_CACHE[key]
     arr = (LqPauliTerm * max(len(terms), 1))()
     L = load()
     for i, (c, s) in enumerate(terms):
         _check(L.lq_pauli_from_string(s.encode(), n, float(c), ctypes.byref(arr[i])))
+    if key is not None:
+        if len(_TERM_CACHE) > 64:
+            _TERM_CACHE.clear()
+        _TERM_CACHE[key] = arr
     return arr
 
 

@@ -340,10 +340,10 @@ __global__ void __launch_bounds__(BLOCK, 3) pass2_kernel(const __grid_constant__
 }
 
 // Tile bits of the reverse sweep: two 32 KiB tiles per CTA (3 CTAs per SM)
-// measured 11% faster than 2^10-amplitude tiles at n = 24 (fewer passes);
-// below n = 20 they would leave SMs idle (2^(n-11) < 2 x 152 tiles), so
-// smaller states keep 2^10-amplitude tiles.
-static int sweep_tile_bits(int n) { return n >= 20 ? 11 : n < 10 ? n : 10; }
+// take fewer passes than 2^10-amplitude tiles: measured 11% faster at
+// n = 24 and 6% at n = 18 (128 tiles); at n = 16 (32 tiles for 152 SMs)
+// 2^10-amplitude tiles are 12% faster.
+static int sweep_tile_bits(int n) { return n >= 18 ? 11 : n < 10 ? n : 10; }
 
 // Largest grid of a two-state pass (the stride of the partial sums): tiles
 // of 2^k amplitudes, up to 6 CTAs per SM; passes with wider tiles launch
