@@ -16,6 +16,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "lq_coefs.h"
@@ -86,10 +89,7 @@ using namespace lq;
 
 extern "C" {
 
-size_t lq_param_shift_workspace_size(int n, int np, int nt, int method) {
-  if (n < 1 || n > 34 || np < 0) return 0;
-  if (method == LQ_PSR_PLAIN)
-    return align256(sizeof(double2) << n) + lq_expval_workspace_size(n, nt);
+static std::size_t batched_workspace_size(int n, int np, int nt) {
   // an HEA-shaped stand-in with np single-use rotations sizes the batch: the
   // workspace depends on n, the number of circuits and the program size
   std::vector<lq_gate> g((std::size_t)np);
@@ -113,6 +113,31 @@ size_t lq_param_shift_workspace_size(int n, int np, int nt, int method) {
   // room for larger op programs than the stand-in: 1 MiB
   return batch_workspace_for(v, nullptr) + ((std::size_t)1 << 20);
 }
+
+size_t lq_param_shift_workspace_size(int n, int np, int nt, int method) {
+  if (n < 1 || n > 34 || np < 0) return 0;
+  if (method == LQ_PSR_PLAIN)
+    return align256(sizeof(double2) << n) + lq_expval_workspace_size(n, nt);
+  // the batched size depends on (n, np, nt) only; planning the stand-in takes
+  // tens to hundreds of microseconds, and every batched call checks its
+  // workspace against it, so sizes are kept
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, std::size_t> sizes;
+  const auto key = std::make_tuple(n, np, nt);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = sizes.find(key);
+    if (it != sizes.end()) return it->second;
+  }
+  const std::size_t sz = batched_workspace_size(n, np, nt);
+  if (sz) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (sizes.size() > 256) sizes.clear();
+    sizes[key] = sz;
+  }
+  return sz;
+}
+
 
 lq_status lq_param_shift_grad(int n, const lq_gate* gates, int ng, const double* params,
                               int np, const lq_pauli_term* terms, int nt, int method,
