@@ -120,3 +120,32 @@ def test_psr_rejects_unsupported_on_host(L):
     st = L.lq_param_shift_grad(2, g, 1, pp, 1, terms, 1, 1, ctypes.byref(e), grp,
                                ctypes.c_void_p(256), 8, None)
     assert st == 4
+
+
+def test_gate_packing_layout_and_cache():
+    """pack_gates fills the lq_gate layout (numpy columns viewed by ctypes),
+    including matrices, and returns the same packing for an equal gate list."""
+    import paper_2512_23183_gb300 as lq
+    import workloads as W
+
+    assert lq._GATE_DTYPE.itemsize == ctypes.sizeof(lq.LqGate)
+    for name, _ctype in lq.LqGate._fields_:
+        assert lq._GATE_DTYPE.fields[name][1] == getattr(lq.LqGate, name).offset, name
+    rng = np.random.default_rng(5)
+    gates, _ = W.random_circuit(6, 40, rng)
+    arr = lq.pack_gates(gates)
+    for i, g in enumerate(gates):
+        assert arr[i].kind == lq.KINDS[g.name]
+        q = list(arr[i].qubits)
+        assert q[: len(g.qubits)] == list(g.qubits) and all(v == -1 for v in q[len(g.qubits):])
+        assert arr[i].param == g.param and arr[i].angle == g.angle
+        if g.mat is not None:
+            m = np.asarray(g.mat, np.complex128).reshape(-1).view(np.float64)
+            assert np.array_equal(np.array(arr[i].mat[: m.size]), m)
+    hea, _ = W.hea(5, 2, "ring")
+    a1 = lq.pack_gates(hea)
+    assert lq.pack_gates(list(hea)) is a1          # equal sequence: kept packing
+    assert lq.pack_gates(hea[:-1]) is not a1
+    t1 = lq.pack_terms(W.heisenberg(5), 5)
+    assert lq.pack_terms(W.heisenberg(5), 5) is t1
+    assert lq.pack_terms(W.heisenberg(5, ring=True), 5) is not t1
