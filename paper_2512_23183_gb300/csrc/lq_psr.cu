@@ -252,7 +252,15 @@ lq_status lq_trotter_evolve(void* amps, int n, const lq_pauli_term* terms, int n
     if (P.xmask == 0) {
       fr = c;
       fi = -s;  // e^{-i phi}
-      if (P.zmask) {
+      if (P.zmask && (P.zmask & (P.zmask - 1)) == 0) {
+        // one Z: e^{-i phi} diag(1, e^{2 i phi}) on its bit, a one-bit phase
+        // that merges with the step's other field terms into one table op
+        o.type = OP_PHASE;
+        o.cm = o.cv = P.zmask;
+        o.a = std::cos(2 * phi);
+        o.b = std::sin(2 * phi);
+        ops.push_back(o);
+      } else if (P.zmask) {
         o.type = OP_PARITY;
         o.z = P.zmask;
         o.a = std::cos(2 * phi);

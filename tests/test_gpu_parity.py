@@ -299,7 +299,7 @@ def test_param_shift_all_two_term_kinds(lq):
 
 # -------------------------------------------------------------- Trotter
 
-@pytest.mark.parametrize("n,steps", [(3, 5), (8, 12), (12, 4)])
+@pytest.mark.parametrize("n,steps", [(3, 5), (8, 12), (12, 4), (16, 3), (20, 2)])
 def test_trotter(lq, n, steps):
     static, field, A, omega, x0 = W.xyz_trotter(n, J=(1.0, 0.7, 0.4))
     dt = 0.07
