@@ -12,9 +12,9 @@
 // The sweep is lowered like a circuit: each U_k^dag becomes tile ops in
 // tangent form with deferred scalars (the same scalar for both states, so
 // <lambda|G|psi> carries the real factor |zeta|^2), and each gradient term
-// becomes an OP_GRAD op reduced per tile; two-state tile passes hold psi and
-// lambda in shared memory together, so each pass reads and writes each
-// state once.  Two states are resident, no checkpoints are needed: U^dag
+// becomes an OP_GRAD op whose per-warp sums collect in shared memory over a
+// CTA's tiles; two-state tile passes hold psi and lambda in shared memory
+// together, so each pass reads and writes each state once.  Two states are resident, no checkpoints are needed: U^dag
 // uncomputes the forward states.
 #include <cuda_runtime.h>
 
