@@ -442,8 +442,8 @@ double op_flops(const LOp& o, int n) {
     case OP_PARITY: return 6.0 * N * 0.5 * frac;
     case OP_SCALE: return ((o.mode & 1) ? 2.0 : 6.0) * N;
     case OP_GRAD: return 4.0 * N;
-    case OP_DPHASE:                                        // (table combine +) multiply
-      return ((o.mode & DP_FULL) ? 6.0 : 12.0) * N * frac;
+    case OP_DPHASE:   // (table combine +) multiply; a butterfly: 6 FMA per pair with its H
+      return ((o.mode & DP_BFLY) ? 8.0 : (o.mode & DP_FULL) ? 6.0 : 12.0) * N * frac;
     case OP_LPHASE:                                        // (table combine +) multiply
       return ((o.mode & LP_TABLE) ? 6.0 : 12.0) * N * frac;
     default: return 0.0;                                   // sign flips, i^k, swaps
@@ -706,21 +706,33 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
         const int c = __builtin_popcount(d.cm_loc);
         if (c < 1) continue;
         const int sz = 1 << (k - c);
-        if (entries + sz > DFULL_MAX_ENTRIES || __builtin_popcount(ubits | d.cm_loc) > 6) continue;
         // the per-tile part commutes to the store if no later op of the pass
         // mixes a condition bit, else to the load if no earlier op does
         bool later = false, earlier = false;
         for (int o2 = o + 1; o2 < cnt; o2++) later |= (op_mixing_bits(P.ops[o2]) & d.cm_loc) != 0;
         for (int o2 = 0; o2 < o; o2++) earlier |= (op_mixing_bits(P.ops[o2]) & d.cm_loc) != 0;
         if (later && earlier) continue;
+        // butterfly with the H on its condition bit right after it (DP_BFLY):
+        // the table is followed by one form byte per entry
+        const bool bfly = later && c == 1 && d.cv_loc == d.cm_loc && d.cm_glob == 0 &&
+                          o + 1 < cnt && P.ops[o + 1].type == OP_H &&
+                          (1u << P.ops[o + 1].b0) == d.cm_loc && P.ops[o + 1].cm_loc == 0 &&
+                          P.ops[o + 1].cm_glob == 0;
+        const int need = sz + (bfly ? (sz + 15) / 16 : 0);
+        if (entries + need > DFULL_MAX_ENTRIES || __builtin_popcount(ubits | d.cm_loc) > 6)
+          continue;
         d.mode |= DP_FULL;
         if (later) {
           d.mode |= DP_PRE;
           P.h.dpre |= (uint8_t)(1u << nd);
         }
+        if (bfly) {
+          d.mode |= DP_BFLY;
+          P.h.flags |= PF_BFLY;
+        }
         d.z_glob = (uint64_t)entries;
         d.b0 = (uint8_t)nd;
-        entries += sz;
+        entries += need;
         ubits |= d.cm_loc;
         nd++;
       }

@@ -377,11 +377,21 @@ __device__ __forceinline__ void build_dfull_table(double2* F, int k, const Op& o
                                                   const double2* __restrict__ dtab) {
   const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull;
   const uint32_t cnt = 1u << (k - __popc(op.cm_loc));
+  unsigned char* form = reinterpret_cast<unsigned char*>(F + cnt);   // DP_BFLY only
   for (uint32_t u = threadIdx.x; u < cnt; u += BLOCK) {
     const uint32_t s = expand(u, op.cm_loc, op.cv_loc);
-    F[u] = dyadic_phase((tb[s & 127] + tb[128 + ((s >> 7) & 127)]) & M34, dtab);
+    const double2 w = dyadic_phase((tb[s & 127] + tb[128 + ((s >> 7) & 127)]) & M34, dtab);
+    if (op.mode & DP_BFLY) {
+      // w = Re w (1 + i Im w / Re w), or w = Im w (1 + i (-Re w / Im w)) i
+      const bool cot = fabs(w.x) < fabs(w.y);
+      F[u] = cot ? make_double2(w.y, -w.x / w.y) : make_double2(w.x, w.y / w.x);
+      form[u] = cot;
+    } else {
+      F[u] = w;
+    }
   }
 }
+
 
 // Per-tile constant of a table-mode OP_DPHASE: the sum of the weights of its
 // `ncta` CTA-decided factors (triples at tr) that hold for the tile's CTA
@@ -402,6 +412,50 @@ struct PassTables {
   const double2* dfull;              // full-mode OP_DPHASE phase tables
   unsigned long long* dfe;           // full mode: this tile's deferred sums
 };
+
+// A DP_BFLY op and the OP_H after it: for each pair (s0, s1 = s0 | 2^c),
+// a' = a + w b, b' = a - w b with w = scale (1 + i s) applied to u = b or
+// u = i b (form byte): t = u (1 + i s) in 2 FMAs, a +- scale t in 4.
+template <int BLOCK>
+__device__ __forceinline__ void dphase_bfly_pairs(double2* __restrict__ sm, uint32_t T,
+                                                  const Op& d, const PassTables* tabs) {
+  const uint32_t tid = threadIdx.x;
+  const uint32_t cnt = T >> 1;
+  const double2* __restrict__ F = tabs->dfull + d.z_glob;
+  const unsigned char* __restrict__ form = reinterpret_cast<const unsigned char*>(F + cnt);
+  const uint32_t xb = d.cm_loc;
+  const int c = __ffs(xb) - 1;
+  auto bfly = [&](double2 A, double2 B, double2 w, unsigned f, double2& o0, double2& o1) {
+    const uint32_t neg = f ? 0x80000000u : 0u;
+    const double ux = f ? xsign(B.y, neg) : B.x, uy = f ? B.x : B.y;
+    const double tx = fma(-w.y, uy, ux), ty = fma(w.y, ux, uy);
+    o0 = make_double2(fma(w.x, tx, A.x), fma(w.x, ty, A.y));
+    o1 = make_double2(fma(-w.x, tx, A.x), fma(-w.x, ty, A.y));
+  };
+  if ((cnt & (2 * BLOCK - 1)) == 0) {
+    for (uint32_t j = tid; j < cnt; j += 2 * BLOCK) {
+      const uint32_t p0 = insert0(j, c), q0 = insert0(j + BLOCK, c);
+      const double2 A = sm[p0], B = sm[p0 | xb], C = sm[q0], D = sm[q0 | xb];
+      const double2 w0 = F[j], w1 = F[j + BLOCK];
+      const unsigned f0 = form[j], f1 = form[j + BLOCK];
+      double2 o0, o1, o2, o3;
+      bfly(A, B, w0, f0, o0, o1);
+      bfly(C, D, w1, f1, o2, o3);
+      sm[p0] = o0;
+      sm[p0 | xb] = o1;
+      sm[q0] = o2;
+      sm[q0 | xb] = o3;
+    }
+  } else {
+    for (uint32_t j = tid; j < cnt; j += BLOCK) {
+      const uint32_t s0 = insert0(j, c);
+      double2 o0, o1;
+      bfly(sm[s0], sm[s0 | xb], F[j], form[j], o0, o1);
+      sm[s0] = o0;
+      sm[s0 | xb] = o1;
+    }
+  }
+}
 
 // Apply one op to a shared-memory tile of T = 2^k amplitudes whose CTA bits
 // are `base`; dtab: the dyadic phase tables; tabs: the pass's per-CTA tables

@@ -96,7 +96,9 @@ constexpr int LPHASE_FAC = 6;      // doubles per OP_LPHASE factor: tile-local c
 constexpr int DYADIC_HALF = 17;    // two-level table: 2^17 + 2^17 entries
 constexpr int MAX_TILE_BITS = 13;   // 2^13 amplitudes = 128 KiB of shared memory
 constexpr int MAX_OPS = 384;        // per pass (kernel-parameter budget)
-constexpr int MAX_COEF = 512;       // doubles per pass coefficient pool
+constexpr int MAX_COEF = 1000;      // doubles per pass coefficient pool (the
+                                    // pass stays within the 32764-byte limit
+                                    // of a kernel parameter)
 
 // Everything a tile pass needs; passed by value as a __grid_constant__
 // kernel parameter (< 32 KiB), so a pass needs no device allocation.
@@ -125,6 +127,8 @@ enum PassFlags : int32_t {
   PF_LTAB = 8,            // ops[ltab_op] is a table-mode OP_LPHASE: its 2^k-entry
                           // phase table is built once per CTA (pass_kernel only)
   PF_DTAB = 16,           // some OP_DPHASE ops are in table mode (pass_kernel only)
+  PF_BFLY = 64,           // some full-mode OP_DPHASE ops run as butterflies with the
+                          // OP_H after them (DP_BFLY; pass_kernel's butterfly variant)
   PF_DFULL = 32,          // some table-mode OP_DPHASE ops use full phase tables and
                           // defer their per-tile phases to the store (pass_kernel only)
 };
@@ -154,6 +158,15 @@ constexpr uint32_t DTAB_MAX_WORDS = 4096;   // per pass (32 KiB of shared memory
 // after the load.
 constexpr uint8_t DP_FULL = 0x40;
 constexpr uint8_t DP_PRE = 0x20;
+// A full-mode, per-tile-part-at-the-load OP_DPHASE on one condition bit c
+// (set) followed by an OP_H on bit c (the inverse gate-form QFT: qubit i's
+// phases, then its H): the two ops form the butterfly (a + w b, a - w b) of
+// the pair (s0, s1 = s0 | 2^c), w the phase of s1 (table entry of the pair
+// index).  Its table holds w as (scale, s) with w = scale (1 + i s) applied
+// to b, or, when |Re w| < |Im w|, w = scale (1 + i s) applied to i b
+// (|s| <= 1 either way), followed by one form byte per entry: 6 FMAs per
+// pair instead of a complex multiply and four adds.
+constexpr uint8_t DP_BFLY = 0x10;
 constexpr int DFULL_MAX_ENTRIES = 3072;     // per pass (48 KiB of shared memory)
 
 // OP_LPHASE in table mode (Op::mode bit): every factor's condition bit is a
@@ -167,6 +180,7 @@ struct PassParams {
   Op ops[MAX_OPS];
   double coef[MAX_COEF];
 };
+static_assert(sizeof(PassParams) <= 32764, "a pass must fit one kernel parameter");
 
 // ----------------------------------------------------- host-side compiler
 

@@ -95,7 +95,9 @@ __device__ __forceinline__ void build_deferred(double2* dD, const PassHeader& h,
   }
 }
 
-template <int BLOCK>
+// BF: the pass has DP_BFLY ops (separate instantiation, so the other passes
+// keep their code and registers).
+template <int BLOCK, bool BF>
 __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ PassParams P,
                                                         double2* __restrict__ state,
                                                         uint64_t stride, int nstates, int dbuf) {
@@ -208,6 +210,14 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
       __syncthreads();
     }
     for (int o = 0; o < nops; o++) {
+      if constexpr (BF) {
+        if (P.ops[o].type == OP_DPHASE && (P.ops[o].mode & DP_BFLY)) {
+          dphase_bfly_pairs<BLOCK>(sm, T, P.ops[o], &tabs);   // with the H after it
+          o++;
+          __syncthreads();
+          continue;
+        }
+      }
       apply_op<BLOCK>(sm, T, P.ops[o], P.coef, base, (const double2*)P.h.dtab, &tabs);
       __syncthreads();
     }
@@ -247,8 +257,13 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
                       ((P.h.flags & PF_DTAB) ? sizeof(double2) * ((P.h.dtab_words + 1) / 2) : 0) +
                       ((P.h.flags & PF_DFULL) ? sizeof(double2) * P.h.dfull_entries : 0);
   cudaError_t ce = once_per_device(configured, [] {
-    return cudaFuncSetAttribute(pass_kernel<kPassBlock>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200u << 10));
+    cudaError_t e = cudaFuncSetAttribute(pass_kernel<kPassBlock, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(200u << 10));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(pass_kernel<kPassBlock, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200u << 10));
+    return e;
   });
   if (ce != cudaSuccess) return ce;
   uint64_t total = P.h.ntiles * (uint64_t)nstates;
@@ -265,9 +280,12 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
     static thread_local PassParams Q;   // launch copy carrying the table address
     Q = P;
     Q.h.dtab = t;
-    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(Q, state, stride, nstates, dbuf);
+    if (P.h.flags & PF_BFLY)
+      pass_kernel<kPassBlock, true><<<grid, kPassBlock, smem, s>>>(Q, state, stride, nstates, dbuf);
+    else
+      pass_kernel<kPassBlock, false><<<grid, kPassBlock, smem, s>>>(Q, state, stride, nstates, dbuf);
   } else {
-    pass_kernel<kPassBlock><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, dbuf);
+    pass_kernel<kPassBlock, false><<<grid, kPassBlock, smem, s>>>(P, state, stride, nstates, dbuf);
   }
   return cudaGetLastError();
 }
