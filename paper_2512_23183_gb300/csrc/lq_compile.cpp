@@ -713,8 +713,10 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
         for (int o2 = 0; o2 < o; o2++) earlier |= (op_mixing_bits(P.ops[o2]) & d.cm_loc) != 0;
         if (later && earlier) continue;
         // butterfly with the H on its condition bit right after it (DP_BFLY):
-        // the table is followed by one form byte per entry
-        const bool bfly = later && c == 1 && d.cv_loc == d.cm_loc && d.cm_glob == 0 &&
+        // the table is followed by one form byte per entry; its per-CTA build
+        // (a division per entry) pays off from 2^12 tiles on (measured:
+        // slower at n = 18-20 with 2^10-amplitude tiles, faster from n = 22)
+        const bool bfly = later && n - k >= 12 && c == 1 && d.cv_loc == d.cm_loc && d.cm_glob == 0 &&
                           o + 1 < cnt && P.ops[o + 1].type == OP_H &&
                           (1u << P.ops[o + 1].b0) == d.cm_loc && P.ops[o + 1].cm_loc == 0 &&
                           P.ops[o + 1].cm_glob == 0;

@@ -329,9 +329,10 @@ static std::vector<int> fft_bounds(int n) {
 // Gates of Alg. 3 without its final swap network.  Alg. 3 applies, for i,
 // H(i) then CP(pi / 2^{j-i}) with control i and target j > i.  CP(i, j) is
 // diagonal: it commutes with every other CP and with the H of any qubit other
-// than i and j, so it can move to just before H(j); the forward list is, for
-// j, the CP(i, j) with i < j, then H(j) -- the same gates, so the same
-// unitary.  Then each qubit's phases (one merged op on its bit) stand right
+// than i and j, so it can move to just before H(j); from n = 24 on the
+// forward list is, for j, the CP(i, j) with i < j, then H(j) -- the same
+// gates, so the same unitary (smaller states keep Alg. 3's order, which
+// schedules into cheaper passes there).  Then each qubit's phases (one merged op on its bit) stand right
 // before its H, which runs them as butterflies (as in the inverse: the
 // reversed Alg. 3 order with conjugated phases).  The floor(n/2)
 // SWAP(i, n-1-i) gates reverse the bits of the index; they run as one
@@ -350,7 +351,7 @@ static std::vector<lq_gate> qft_gate_list(int n, int inverse) {
     G.angle = ang;
     return G;
   };
-  if (!inverse) {
+  if (!inverse && n >= 24) {   // measured: from n = 24 on the reordered list is faster
     for (int j = 0; j < n; j++) {
       for (int i = 0; i < j; i++) g.push_back(mk(LQ_CP, i, j, PI / std::ldexp(1.0, j - i)));
       g.push_back(mk(LQ_H, j, -1, 0));

@@ -257,6 +257,21 @@ def test_qft_gate_form(lq, n):
 
 
 @pytest.mark.parametrize("n", [22, 24])
+def test_qft_gate_form_large_against_fft_form(lq, n):
+    # from 2^12 tiles on the gate form runs butterflies, and from n = 24 the
+    # forward list has each CP moved before its target's H: both forms agree
+    # element-wise (the FFT form is pinned to the oracle), and the inverse
+    # gate form undoes the forward FFT form
+    psi = W.gaussian_state(n, 3000 + n)
+    a, b = dev(psi), dev(psi)
+    lq.qft(a, n, method=lq.QFT_GATES)
+    lq.qft(b, n, method=lq.QFT_FFT)
+    assert float((a - b).abs().max()) < ATOL
+    lq.qft(b, n, inverse=True, method=lq.QFT_GATES)
+    np.testing.assert_allclose(host(b), psi, rtol=0, atol=ATOL)
+
+
+@pytest.mark.parametrize("n", [22, 24])
 def test_qft_basis_closed_form_sampled(lq, n):
     N = 1 << n
     x = W.basis_index(n, 2000 + n)
