@@ -716,11 +716,28 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
         // the table is followed by one form byte per entry; its per-CTA build
         // (a division per entry) pays off from 2^12 tiles on (measured:
         // slower at n = 18-20 with 2^10-amplitude tiles, faster from n = 22)
-        const bool bfly = later && n - k >= 12 && c == 1 && d.cv_loc == d.cm_loc && d.cm_glob == 0 &&
-                          o + 1 < cnt && P.ops[o + 1].type == OP_H &&
-                          (1u << P.ops[o + 1].b0) == d.cm_loc && P.ops[o + 1].cm_loc == 0 &&
-                          P.ops[o + 1].cm_glob == 0;
-        const int need = sz + (bfly ? (sz + 15) / 16 : 0);
+        bool bfly = later && n - k >= 12 && c == 1 && d.cv_loc == d.cm_loc && d.cm_glob == 0 &&
+                    o + 1 < cnt && P.ops[o + 1].type == OP_H &&
+                    (1u << P.ops[o + 1].b0) == d.cm_loc && P.ops[o + 1].cm_loc == 0 &&
+                    P.ops[o + 1].cm_glob == 0;
+        // a butterfly's phase depends on its factors' tile bits only: when
+        // they form one run [lo, lo + width) of tile-local positions (both
+        // QFT directions), its table is indexed by that run alone
+        int bsz = sz, lo = 0, width = k - c;
+        if (bfly) {
+          uint32_t fl = 0;
+          const double* Fc = P.coef + d.cidx;
+          for (uint32_t f = 0; f < d.x_loc; f++) fl |= (uint32_t)dbits(Fc[4 * f]) & ~d.cm_loc;
+          if (fl == 0) {
+            width = 0;
+          } else {
+            lo = __builtin_ctz(fl);
+            width = 32 - __builtin_clz(fl) - lo;
+            if (fl != (((1u << width) - 1u) << lo)) bfly = false;   // not one run
+          }
+          if (bfly) bsz = 1 << width;
+        }
+        const int need = bfly ? bsz + (bsz + 15) / 16 : sz;
         if (entries + need > DFULL_MAX_ENTRIES || __builtin_popcount(ubits | d.cm_loc) > 6)
           continue;
         d.mode |= DP_FULL;
@@ -731,6 +748,8 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
         if (bfly) {
           d.mode |= DP_BFLY;
           P.h.flags |= PF_BFLY;
+          d.a = lo;      // table index = (s >> lo) & (2^width - 1)
+          d.b = width;
         }
         d.z_glob = (uint64_t)entries;
         d.b0 = (uint8_t)nd;

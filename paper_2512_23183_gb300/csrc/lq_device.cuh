@@ -376,12 +376,15 @@ __device__ __forceinline__ void build_dfull_table(double2* F, int k, const Op& o
                                                   const unsigned long long* tb,
                                                   const double2* __restrict__ dtab) {
   const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull;
-  const uint32_t cnt = 1u << (k - __popc(op.cm_loc));
+  const bool bf = (op.mode & DP_BFLY) != 0;
+  const int lo = bf ? (int)op.a : 0;
+  const uint32_t cnt = bf ? 1u << (int)op.b : 1u << (k - __popc(op.cm_loc));
   unsigned char* form = reinterpret_cast<unsigned char*>(F + cnt);   // DP_BFLY only
   for (uint32_t u = threadIdx.x; u < cnt; u += BLOCK) {
-    const uint32_t s = expand(u, op.cm_loc, op.cv_loc);
+    // butterflies: the factor bits' run at u, the condition bit set
+    const uint32_t s = bf ? (u << lo) | op.cm_loc : expand(u, op.cm_loc, op.cv_loc);
     const double2 w = dyadic_phase((tb[s & 127] + tb[128 + ((s >> 7) & 127)]) & M34, dtab);
-    if (op.mode & DP_BFLY) {
+    if (bf) {
       // w = Re w (1 + i Im w / Re w), or w = Im w (1 + i (-Re w / Im w)) i
       const bool cot = fabs(w.x) < fabs(w.y);
       F[u] = cot ? make_double2(w.y, -w.x / w.y) : make_double2(w.x, w.y / w.x);
@@ -415,14 +418,18 @@ struct PassTables {
 
 // A DP_BFLY op and the OP_H after it: for each pair (s0, s1 = s0 | 2^c),
 // a' = a + w b, b' = a - w b with w = scale (1 + i s) applied to u = b or
-// u = i b (form byte): t = u (1 + i s) in 2 FMAs, a +- scale t in 4.
+// u = i b (form byte): t = u (1 + i s) in 2 FMAs, a +- scale t in 4.  The
+// table index is the pair's factor-bit run (s0 >> a) mod 2^b (the condition
+// bit c lies outside the run).
 template <int BLOCK>
 __device__ __forceinline__ void dphase_bfly_pairs(double2* __restrict__ sm, uint32_t T,
                                                   const Op& d, const PassTables* tabs) {
   const uint32_t tid = threadIdx.x;
   const uint32_t cnt = T >> 1;
+  const int lo = (int)d.a;
+  const uint32_t tmask = (1u << (int)d.b) - 1u;   // table: 2^b entries, then form bytes
   const double2* __restrict__ F = tabs->dfull + d.z_glob;
-  const unsigned char* __restrict__ form = reinterpret_cast<const unsigned char*>(F + cnt);
+  const unsigned char* __restrict__ form = reinterpret_cast<const unsigned char*>(F + tmask + 1);
   const uint32_t xb = d.cm_loc;
   const int c = __ffs(xb) - 1;
   auto bfly = [&](double2 A, double2 B, double2 w, unsigned f, double2& o0, double2& o1) {
@@ -436,8 +443,9 @@ __device__ __forceinline__ void dphase_bfly_pairs(double2* __restrict__ sm, uint
     for (uint32_t j = tid; j < cnt; j += 2 * BLOCK) {
       const uint32_t p0 = insert0(j, c), q0 = insert0(j + BLOCK, c);
       const double2 A = sm[p0], B = sm[p0 | xb], C = sm[q0], D = sm[q0 | xb];
-      const double2 w0 = F[j], w1 = F[j + BLOCK];
-      const unsigned f0 = form[j], f1 = form[j + BLOCK];
+      const uint32_t i0 = (p0 >> lo) & tmask, i1 = (q0 >> lo) & tmask;
+      const double2 w0 = F[i0], w1 = F[i1];
+      const unsigned f0 = form[i0], f1 = form[i1];
       double2 o0, o1, o2, o3;
       bfly(A, B, w0, f0, o0, o1);
       bfly(C, D, w1, f1, o2, o3);
@@ -448,9 +456,9 @@ __device__ __forceinline__ void dphase_bfly_pairs(double2* __restrict__ sm, uint
     }
   } else {
     for (uint32_t j = tid; j < cnt; j += BLOCK) {
-      const uint32_t s0 = insert0(j, c);
+      const uint32_t s0 = insert0(j, c), i0 = (s0 >> lo) & tmask;
       double2 o0, o1;
-      bfly(sm[s0], sm[s0 | xb], F[j], form[j], o0, o1);
+      bfly(sm[s0], sm[s0 | xb], F[i0], form[i0], o0, o1);
       sm[s0] = o0;
       sm[s0 | xb] = o1;
     }

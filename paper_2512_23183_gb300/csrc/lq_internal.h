@@ -165,7 +165,9 @@ constexpr uint8_t DP_PRE = 0x20;
 // index).  Its table holds w as (scale, s) with w = scale (1 + i s) applied
 // to b, or, when |Re w| < |Im w|, w = scale (1 + i s) applied to i b
 // (|s| <= 1 either way), followed by one form byte per entry: 6 FMAs per
-// pair instead of a complex multiply and four adds.
+// pair instead of a complex multiply and four adds.  The phase depends on the
+// factors' tile bits only, which form one run of tile-local positions
+// [a, a + b) (Op::a, Op::b): the table has 2^b entries, index (s >> a) mod 2^b.
 constexpr uint8_t DP_BFLY = 0x10;
 constexpr int DFULL_MAX_ENTRIES = 3072;     // per pass (48 KiB of shared memory)
 
