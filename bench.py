@@ -358,7 +358,7 @@ def bench_lq(a, rank, world, device):
                 "flops_note": "achieved counts the plans' flops (FMA = 2, add/multiply = 1); "
                               "a DADD or DMUL takes an FP64 issue slot like a DFMA, so the "
                               "FP64-pipe activity ncu measures is higher: 80-85% on the HEA "
-                              "passes, 76% on the gate-form QFT passes "
+                              "passes, 82-83% on the gate-form QFT passes "
                               "(profiles/pass_kernel_n24.md)",
                 "hbm": {"achieved_gbs": round(ach_gbs, 1), "peak_gbs": hbm_peak,
                         "frac": round(ach_gbs / hbm_peak, 4),
