@@ -548,8 +548,14 @@ static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef
 lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, double zi,
                        const ScheduleOptions& opt, Schedule& out) {
   const int k = opt.k < n ? opt.k : n;
-  const int m = opt.m < k ? opt.m : k;
+  int m = opt.m < k ? opt.m : k;
   if (k > MAX_TILE_BITS || k < 1) return fail(LQ_ERR_INVALID_ARG, "tile bits %d", k);
+  // the kernels map the tile bits above the low run through a table of
+  // 2^max_hi offsets: a smaller low run is widened to fit it
+  if (opt.max_hi < 0) return fail(LQ_ERR_INVALID_ARG, "internal: max_hi %d", opt.max_hi);
+  if (k - m > opt.max_hi) m = k - opt.max_hi;
+  // pass_kernel keeps those offsets shifted right by the low run in 32 bits
+  if (m < n - 32) m = n - 32;
   const uint64_t low = (m >= 64) ? ~0ull : ((1ull << m) - 1);
   const bool need_scale = opt.force_scale || !(zr == 1.0 && zi == 0.0);
 

@@ -95,6 +95,8 @@ constexpr int LPHASE_FAC = 6;      // doubles per OP_LPHASE factor: tile-local c
                                    // CTA cm, CTA cv, re, im, source gate
 constexpr int DYADIC_HALF = 17;    // two-level table: 2^17 + 2^17 entries
 constexpr int MAX_TILE_BITS = 13;   // 2^13 amplitudes = 128 KiB of shared memory
+constexpr int PASS_HI_BITS = 9;    // pass_kernel maps up to 9 tile bits above the
+                                   // contiguous low run (a 512-entry offset table)
 constexpr int MAX_OPS = 384;        // per pass (kernel-parameter budget)
 constexpr int MAX_COEF = 1000;      // doubles per pass coefficient pool (the
                                     // pass stays within the 32764-byte limit
@@ -223,7 +225,11 @@ lq_status lower_gate(const lq_gate& g, int n, double theta, Lowered& out);
 // Pass schedule: one PassParams per tile pass, in execution order.
 struct ScheduleOptions {
   int k = 10;                // tile bits
-  int m = 5;                 // contiguous low bits always in the tile
+  int m = 5;                 // contiguous low bits always in the tile (raised
+                             // to k - max_hi when smaller)
+  int max_hi = 8;            // tile bits above the low run that the launching
+                             // kernel's offset table maps (2^max_hi entries;
+                             // pass_kernel: PASS_HI_BITS)
   bool force_scale = false;  // always end with a (final) OP_SCALE
   bool merge_params = true;  // merge one-bit phases of parametrised gates too
   int max_grads = 1 << 30;   // OP_GRAD ops per pass (two-state passes keep a

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
                                                         double2* __restrict__ state,
                                                         uint64_t stride, int nstates, int dbuf) {
   extern __shared__ double2 smem_tiles[];
-  __shared__ uint32_t hioff[256];   // high tile bits' global offsets >> m
+  __shared__ uint32_t hioff[1 << PASS_HI_BITS];   // high tile bits' global offsets >> m
   const int k = P.h.k, m = P.h.m, nops = P.h.nops;
   const uint32_t T = 1u << k;
   const uint32_t lowmask = (1u << m) - 1u;

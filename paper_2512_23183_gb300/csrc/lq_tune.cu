@@ -153,8 +153,11 @@ lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng
   };
   std::vector<Cand> cands;
   const int kmax = n < MAX_TILE_BITS - 1 ? n : MAX_TILE_BITS - 1;   // up to 2^12
+  // low runs of 5 and 6 bits; with 2^12 tiles also 3 and 4 (more high bits
+  // per pass: an n = 30 layer of one-qubit rotations takes 3 passes at
+  // m = 3 instead of 4 at m = 5)
   for (int k = kmax < 9 ? kmax : 9; k <= kmax; k++)
-    for (int m = 5; m <= 6; m++)
+    for (int m = k >= 12 ? 3 : 5; m <= 6; m++)
       for (int table = 1; table >= 0; table--) {
         const int mm = m < k ? m : k;
         bool dup = false;
@@ -168,6 +171,7 @@ lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng
     ScheduleOptions opt;
     opt.k = c.k;
     opt.m = c.m;
+    opt.max_hi = PASS_HI_BITS;
     opt.lphase_table = c.table != 0;
     Schedule S;
     st = schedule_ops(n, ops, nops, zr, zi, opt, S);

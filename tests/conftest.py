@@ -1,4 +1,5 @@
 import os
+import struct
 import sys
 
 import pytest
@@ -29,3 +30,52 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def _gpu_key():
+    """The autotune cache's device key: "<name>|<SM count>" of the current
+    device, or "unknown" without one."""
+    import torch
+
+    if not torch.cuda.is_available():
+        return "unknown"
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return p.name.replace(" ", "_").replace("\t", "_") + "|%d" % p.multi_processor_count
+
+
+def _structure_hash(n, packed):
+    """FNV-1a (64-bit) over n and each gate's (kind, qubits, has-parameter)
+    record, plus the angle of a gate without a parameter: the cache's key for
+    a circuit structure (gates with a matrix are not handled here)."""
+    h = 1469598103934665603
+
+    def fnv(h, data):
+        for byte in data:
+            h ^= byte
+            h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+        return h
+
+    h = fnv(h, struct.pack("<i", n))
+    for g in packed:
+        h = fnv(h, struct.pack("<5i", g.kind, g.qubits[0], g.qubits[1], g.qubits[2],
+                               1 if g.param >= 0 else 0))
+        if g.param < 0:
+            h = fnv(h, struct.pack("<d", g.angle))
+    return h
+
+
+@pytest.fixture()
+def tune_entry(tmp_path):
+    """Replace the autotune cache by one entry (k, m, table) for this circuit
+    structure on the current device, through the cache file loader."""
+    import paper_2512_23183_gb300 as lq
+
+    def put(n, gates, k, m, table):
+        lq.tune_cache_clear()
+        f = tmp_path / "entry.txt"
+        f.write_text("%s %d %016x %d %d %d 1.0 2.0\n"
+                     % (_gpu_key(), n, _structure_hash(n, lq.pack_gates(gates)), k, m, table))
+        lq.tune_cache_load(str(f))
+
+    yield put
+    lq.tune_cache_clear()

@@ -34,7 +34,8 @@ def test_autotune_choice_and_parity(lq, n, depth, tmp_path):
     gates, P = W.hea(n, depth, "ring")
     r = lq.autotune(n, gates, W.angles(P, 3))
     assert r["candidates"] >= 4
-    assert 9 <= r["tile_bits"] <= 12 and r["low_bits"] in (5, 6)
+    assert 9 <= r["tile_bits"] <= 12 and r["low_bits"] in (3, 4, 5, 6)
+    assert r["low_bits"] >= 5 or r["tile_bits"] == 12   # short low runs with 2^12 tiles only
     assert r["ms"] <= r["ms_default"]
     assert lq.circuit_plan(n, gates, W.angles(P, 4))["tile_bits"] == r["tile_bits"]
     # the tuned schedule serves other parameter values of the same structure
@@ -52,6 +53,24 @@ def test_autotune_choice_and_parity(lq, n, depth, tmp_path):
     assert lq.tune_cache_size() == 0
     lq.tune_cache_load(str(f))
     assert lq.circuit_plan(n, gates, W.angles(P, 4))["tile_bits"] == r["tile_bits"]
+
+
+@pytest.mark.parametrize("m", [1, 3, 4])
+def test_short_low_runs_parity(lq, tune_entry, m):
+    """Schedules with 2^12 tiles and short contiguous low runs (m = 1 is
+    widened to 3 by the pass kernel's 9-bit offset table): 2^9 tiles of an
+    n = 21 state whose passes map up to 9 tile bits above the low run,
+    results equal to the oracle's."""
+    n = 21
+    gates, P = W.hea(n, 2, "ring")
+    tune_entry(n, gates, 12, m, 0)
+    assert lq.circuit_plan(n, gates, W.angles(P, 7))["tile_bits"] == 12
+    th = W.angles(P, 7)
+    psi = W.gaussian_state(n, 11)
+    t = _dev(psi)
+    lq.apply_circuit(t, n, gates, th)
+    want = oracle.apply_circuit(psi.copy(), n, gates, th)
+    np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
 
 
 def test_autotune_qft_gate_circuit(lq):

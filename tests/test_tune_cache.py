@@ -64,3 +64,24 @@ def test_plan_unaffected_by_other_gpus_entries(L, tmp_path):
     f.write_text("Some_Other_GPU|1 16 %016x 12 6 0 1.0 2.0\n" % 0x1234)
     lq.tune_cache_load(str(f))
     assert lq.circuit_plan(n, gates, W.angles(P, 1)) == before
+
+
+def test_low_run_widened_to_the_offset_table(L, tmp_path, tune_entry):
+    """A cached low run that leaves more tile bits above it than the pass
+    kernel's offset table maps (9) is widened: k = 12 with m = 1 plans as
+    m = 3.  With 2^12 tiles an n = 30 layer of one-qubit rotations and a CNOT
+    ladder takes 3 passes at m = 3 (12 + 9 + 9 qubits) and 4 at m = 5."""
+    import workloads as W
+
+    n = 30
+    gates, P = W.hea(n, 1, "ladder")
+    th = W.angles(P, 1)
+
+    def plan_with(m):
+        tune_entry(n, gates, 12, m, 0)
+        return lq.circuit_plan(n, gates, th)
+
+    p1, p3, p5 = plan_with(1), plan_with(3), plan_with(5)
+    assert p3["tile_bits"] == 12 and p5["tile_bits"] == 12   # the entry applies
+    assert p1 == p3
+    assert p3["npasses"] == 3 and p5["npasses"] == 4
