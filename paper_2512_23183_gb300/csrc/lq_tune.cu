@@ -153,11 +153,12 @@ lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng
   };
   std::vector<Cand> cands;
   const int kmax = n < MAX_TILE_BITS - 1 ? n : MAX_TILE_BITS - 1;   // up to 2^12
-  // low runs of 5 and 6 bits; with 2^12 tiles also 3 and 4 (more high bits
-  // per pass: an n = 30 layer of one-qubit rotations takes 3 passes at
-  // m = 3 instead of 4 at m = 5)
+  // low runs of 5 and 6 bits; with 2^11 and 2^12 tiles also 3 and 4 (more
+  // high bits per pass: at n = 30 a layer of one-qubit rotations takes 3
+  // passes at k = 12, m = 3 instead of 4 at m = 5, the inverse gate-form QFT
+  // 4 at k = 11, m = 4 instead of 5 at m = 5)
   for (int k = kmax < 9 ? kmax : 9; k <= kmax; k++)
-    for (int m = k >= 12 ? 3 : 5; m <= 6; m++)
+    for (int m = k >= 11 ? 3 : 5; m <= 6; m++)
       for (int table = 1; table >= 0; table--) {
         const int mm = m < k ? m : k;
         bool dup = false;

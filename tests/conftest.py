@@ -64,6 +64,24 @@ def _structure_hash(n, packed):
     return h
 
 
+def inverse_qft_gates(n):
+    """The gate list the library schedules for the inverse gate-form QFT:
+    Alg. 3 (H(i), then CP(pi / 2^(j-i)) from control i to each j > i) in
+    reverse order with negated angles, without the swap network (one
+    bit-reversal pass)."""
+    import math
+
+    import workloads as W
+
+    g = []
+    for i in range(n):
+        g.append(W.G("H", i))
+        for j in range(i + 1, n):
+            g.append(W.G("CP", i, j, angle=math.pi / 2.0 ** (j - i)))
+    return [W.G("CP", x.qubits[0], x.qubits[1], angle=-x.angle) if x.name == "CP" else x
+            for x in reversed(g)]
+
+
 @pytest.fixture()
 def tune_entry(tmp_path):
     """Replace the autotune cache by one entry (k, m, table) for this circuit

@@ -35,7 +35,7 @@ def test_autotune_choice_and_parity(lq, n, depth, tmp_path):
     r = lq.autotune(n, gates, W.angles(P, 3))
     assert r["candidates"] >= 4
     assert 9 <= r["tile_bits"] <= 12 and r["low_bits"] in (3, 4, 5, 6)
-    assert r["low_bits"] >= 5 or r["tile_bits"] == 12   # short low runs with 2^12 tiles only
+    assert r["low_bits"] >= 5 or r["tile_bits"] >= 11   # short low runs with 2^11, 2^12 tiles
     assert r["ms"] <= r["ms_default"]
     assert lq.circuit_plan(n, gates, W.angles(P, 4))["tile_bits"] == r["tile_bits"]
     # the tuned schedule serves other parameter values of the same structure
@@ -70,6 +70,22 @@ def test_short_low_runs_parity(lq, tune_entry, m):
     t = _dev(psi)
     lq.apply_circuit(t, n, gates, th)
     want = oracle.apply_circuit(psi.copy(), n, gates, th)
+    np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
+
+
+@pytest.mark.parametrize("m", [3, 4])
+def test_short_low_runs_inverse_gate_qft(lq, tune_entry, m):
+    """The inverse gate-form QFT (butterfly passes) with 2^11 tiles and a 3-
+    or 4-bit low run, n = 22: equal to the oracle's inverse DFT."""
+    from conftest import inverse_qft_gates
+
+    n = 22
+    tune_entry(n, inverse_qft_gates(n), 11, m, 1)
+    assert lq.qft_plan(n, lq.QFT_GATES, inverse=True)["tile_bits"] == 11
+    psi = W.gaussian_state(n, 5000 + m)
+    t = _dev(psi)
+    lq.qft(t, n, inverse=True, method=lq.QFT_GATES)
+    want = oracle.qft_fft(psi.copy(), n, inverse=True)
     np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
 
 

@@ -85,3 +85,20 @@ def test_low_run_widened_to_the_offset_table(L, tmp_path, tune_entry):
     assert p3["tile_bits"] == 12 and p5["tile_bits"] == 12   # the entry applies
     assert p1 == p3
     assert p3["npasses"] == 3 and p5["npasses"] == 4
+
+
+def test_short_low_run_for_the_inverse_gate_qft(L, tune_entry):
+    """The inverse gate-form QFT at n = 30: with 2^11 tiles a 4-bit low run
+    leaves 7 new qubits per pass (11 + 7 + 7 + 5: 4 passes) where a 5-bit run
+    leaves 6 (5 passes); the plan adds the bit-reversal pass.  The entry is
+    keyed by the structure of the gate list the library builds."""
+    from conftest import inverse_qft_gates
+
+    n = 30
+    g = inverse_qft_gates(n)
+    tune_entry(n, g, 11, 4, 1)
+    p4 = lq.qft_plan(n, lq.QFT_GATES, inverse=True)
+    tune_entry(n, g, 11, 5, 1)
+    p5 = lq.qft_plan(n, lq.QFT_GATES, inverse=True)
+    assert p4["tile_bits"] == p5["tile_bits"] == 11
+    assert p4["npasses"] == 4 + 1 and p5["npasses"] == 5 + 1
