@@ -357,7 +357,7 @@ def bench_lq(a, rank, world, device):
                              % FP64_MEASURED_TFLOPS,
                 "flops_note": "achieved counts the plans' flops (FMA = 2, add/multiply = 1); "
                               "a DADD or DMUL takes an FP64 issue slot like a DFMA, so the "
-                              "FP64-pipe activity ncu measures is higher: 80-85% on the HEA "
+                              "FP64-pipe activity ncu measures is higher: 83-85% on the HEA "
                               "passes, 82-83% on the gate-form QFT passes "
                               "(profiles/pass_kernel_n24.md)",
                 "hbm": {"achieved_gbs": round(ach_gbs, 1), "peak_gbs": hbm_peak,
