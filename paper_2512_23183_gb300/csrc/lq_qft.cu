@@ -246,31 +246,40 @@ cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, 
 // high L bits; the middle bits M select the tile.  Tile c and tile rev_M(c)
 // exchange contents, so one CTA handles the pair (c <= rev_M(c)) and no tile
 // is read after another CTA wrote it.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) bitrev_kernel(double2* __restrict__ state, int n,
-                                                       int L) {
+template <int BLOCK, int L>
+__global__ void __launch_bounds__(BLOCK) bitrev_kernel(double2* __restrict__ state, int n) {
   extern __shared__ double2 sm[];  // 2 * 2^{2L}
+  constexpr uint32_t TL = 1u << L, T = TL * TL;
+  static_assert(L >= 3, "the swizzle takes 3 row bits");
   const int M = n - 2 * L;
-  const uint32_t TL = 1u << L, T = TL * TL;
   double2* A = sm;
   double2* B = sm + T;
   const uint64_t ntiles = 1ull << M;
+  // Tile rows are stored XOR-swizzled: (row r, column col) at r * TL + (col ^
+  // ((r >> (L - 3)) & 7)).  The transposed read below takes rows r = rev(lo2)
+  // for 8 consecutive lo2 per quarter warp; those rows differ exactly in bits
+  // L-3..L-1, so the 8 accesses hit 8 different 16-byte bank slots (without
+  // the swizzle all 8 hit the same one).
   for (uint64_t c = blockIdx.x; c < ntiles; c += gridDim.x) {
     const uint64_t cr = M ? (__brevll(c) >> (64 - M)) : 0;
     if (cr < c) continue;
-    // element (hi, lo) of tile c: index hi << (n-L) | c << L | lo; slot hi*TL+lo
+    // element (hi, lo) of tile c: index hi << (n-L) | c << L | lo
+#pragma unroll 4
     for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
-      const uint64_t hi = s >> L, lo = s & (TL - 1);
-      A[s] = state[(hi << (n - L)) | (c << L) | lo];
-      if (cr != c) B[s] = state[(hi << (n - L)) | (cr << L) | lo];
+      const uint32_t hi = s >> L, lo = s & (TL - 1);
+      const uint32_t slot = hi * TL + (lo ^ ((hi >> (L - 3)) & 7u));
+      A[slot] = state[((uint64_t)hi << (n - L)) | (c << L) | lo];
+      if (cr != c) B[slot] = state[((uint64_t)hi << (n - L)) | (cr << L) | lo];
     }
     __syncthreads();
     // destination (hi', lo') of tile cr receives source (hi = rev(lo'), lo = rev(hi'))
+#pragma unroll 4
     for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
       const uint32_t hi2 = s >> L, lo2 = s & (TL - 1);
-      const uint32_t src = ((__brev(lo2) >> (32 - L)) << L) | (__brev(hi2) >> (32 - L));
-      state[((uint64_t)hi2 << (n - L)) | (cr << L) | lo2] = A[src];
-      if (cr != c) state[((uint64_t)hi2 << (n - L)) | (c << L) | lo2] = B[src];
+      const uint32_t r = __brev(lo2) >> (32 - L), col = __brev(hi2) >> (32 - L);
+      const uint32_t slot = r * TL + (col ^ ((r >> (L - 3)) & 7u));
+      state[((uint64_t)hi2 << (n - L)) | (cr << L) | lo2] = A[slot];
+      if (cr != c) state[((uint64_t)hi2 << (n - L)) | (c << L) | lo2] = B[slot];
     }
     __syncthreads();
   }
@@ -298,12 +307,14 @@ cudaError_t launch_bitrev(double2* state, int n, cudaStream_t s) {
     bitrev_small_kernel<<<1, 512, sizeof(double2) << n, s>>>(state, n);
     return cudaGetLastError();
   }
-  const int L = 5;
+  // 32 x 32 tiles (512-byte runs), 32 KiB of shared memory per CTA: six
+  // CTAs per SM (measured at n = 30: 6.6 ms against 8.0 ms with four)
+  constexpr int L = 5;
   size_t smem = 2 * (sizeof(double2) << (2 * L));
   uint64_t ntiles = 1ull << (n - 2 * L);
-  uint64_t cap = (uint64_t)sm_count() * 4;
+  uint64_t cap = (uint64_t)sm_count() * 6;
   int grid = (int)(ntiles < cap ? ntiles : cap);
-  bitrev_kernel<256><<<grid, 256, smem, s>>>(state, n, L);
+  bitrev_kernel<256, L><<<grid, 256, smem, s>>>(state, n);
   return cudaGetLastError();
 }
 
