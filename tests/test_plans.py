@@ -1,0 +1,54 @@
+"""Pass structure of the bench's rows, from the host-side plans (no GPU):
+how many state passes each row takes and the bytes it moves, at the sizes
+the bench runs.  The counts follow from the tile geometry alone."""
+import pytest
+
+import paper_2512_23183_gb300 as lq
+import workloads as W
+
+
+@pytest.fixture(scope="module", autouse=True)
+def L():
+    lib = lq.load()
+    lq.tune_cache_clear()
+    yield lib
+
+
+def test_hea_layer_default_schedule_n30():
+    # default tiles: k = 10 with the 5 low bits always in the tile, so each
+    # pass brings 5 new qubits and the last one 10: 5 + 5 + 5 + 5 + 10 = 30
+    n = 30
+    gates, P = W.hea(n, 1, "ladder")
+    p = lq.circuit_plan(n, gates, W.angles(P, 1))
+    assert p["tile_bits"] == 10 and p["npasses"] == 5
+    assert p["dram_bytes"] == 5 * 32 * 2.0 ** n
+
+
+@pytest.mark.parametrize("n,passes", [(20, 2), (24, 3), (30, 3)])
+def test_fft_qft_passes(n, passes):
+    # groups of at most 10 qubits, the last (lowest) of at most 12, plus the
+    # bit-reversal pass; each pass reads and writes the state once
+    p = lq.qft_plan(n, lq.QFT_FFT)
+    assert p["npasses"] == passes + 1
+    assert p["dram_bytes"] == (passes + 1) * 32 * 2.0 ** n
+
+
+@pytest.mark.parametrize("n,reads", [(24, 3), (30, 4)])
+def test_xyz_chain_expval_reads(n, reads):
+    # 3(n-1) terms: one diagonal group (ZZ) and n-1 X-mask groups (XX+YY on a
+    # bond); a tile holds 12 bits, the 5 low ones fixed, so a pass covers the
+    # bonds inside 7 further bits
+    terms = W.heisenberg(n)
+    assert len(terms) == 3 * (n - 1)
+    p = lq.expval_plan(n, terms)
+    assert p["npasses"] == reads
+    assert p["dram_bytes"] == reads * 16 * 2.0 ** n
+
+
+def test_inverse_gate_qft_default_schedule_n30():
+    # the phases need no tile bits; the 30 H do: with k = 10 and 5 fixed low
+    # bits, 5 + 5 + 5 + 5 + 10 qubits in 5 passes, then the bit reversal
+    n = 30
+    p = lq.qft_plan(n, lq.QFT_GATES, inverse=True)
+    assert p["tile_bits"] == 10 and p["npasses"] == 5 + 1
+    assert p["dram_bytes"] == 6 * 32 * 2.0 ** n
