@@ -368,8 +368,8 @@ lq_status lq_vqe_adam(int n, const lq_gate* gates, int ng, double* params, int n
                       lq_stream stream);
 
 /* ---------------------------------------------------------------------------
- * Serving: a continuous-batching request server (spec addition; the
- * paper has no serving layer).  Requests carry one circuit, its parameters
+ * Serving: a continuous-batching request server (an addition: the paper
+ * has no serving layer).  Requests carry one circuit, its parameters
  * and a Pauli sum, energy only or energy and gradient (adjoint).  The server
  * admits a request when its footprint (lq_server_footprint) fits in the free
  * part of the caller's device arena and a worker slot is free; work of
