@@ -159,7 +159,9 @@ lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng
   // 4 at k = 11, m = 4 instead of 5 at m = 5)
   for (int k = kmax < 9 ? kmax : 9; k <= kmax; k++)
     for (int m = k >= 11 ? 3 : 5; m <= 6; m++)
-      for (int table = 1; table >= 0; table--) {
+      // the per-CTA phase table exists for tiles of up to 2^LTAB_MAX_BITS
+      // amplitudes; above that both settings give the same schedule
+      for (int table = k <= LTAB_MAX_BITS ? 1 : 0; table >= 0; table--) {
         const int mm = m < k ? m : k;
         bool dup = false;
         for (const Cand& c : cands) dup |= c.k == k && c.m == mm && c.table == table;
