@@ -17,7 +17,13 @@
  *   - work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
  *     stream); calls are asynchronous unless they return host values, in which
  *     case they synchronise `stream` before returning;
- *   - sizes: 1 <= n <= 34 qubits.
+ *   - sizes: 1 <= n <= 34 qubits;
+ *   - constant device tables (dyadic phases for merged phase gates, QFT
+ *     twiddles) are filled once per device by the first call that needs
+ *     them, on a private stream that the call waits for, so a first call on
+ *     any thread or stream sees complete tables; that first fill is refused
+ *     with LQ_ERR_CUDA when `stream` is being captured into a CUDA graph:
+ *     make one uncaptured call of the same kind on each device first.
  *
  * Validation stands in for the compile-time checks of Sec. III-B
  * (parameter bounds, parametrised versus fixed gates):
@@ -123,6 +129,16 @@ const char* lq_last_error(void);
 
 /* Library version string. */
 const char* lq_version(void);
+
+/* Measured FP64 FMA throughput of the current device, in TFLOP/s (an FMA
+ * counts 2 flops): `reps` timed launches (after one warm-up) of a kernel of
+ * independent DFMA chains with no memory traffic, filling every SM, timed
+ * with CUDA events on `stream`; the best launch is reported (and its
+ * milliseconds in *ms_best when not NULL).  The roofline denominator of the
+ * FP64-bound kernels (no paper counterpart: measurement only).  Allocates
+ * nothing; synchronises `stream`.  LQ_ERR_INVALID_ARG for reps outside
+ * [1, 1000] or a NULL tflops. */
+lq_status lq_measure_fp64_fma(int reps, double* tflops, double* ms_best, lq_stream stream);
 
 /* Parse a Pauli string (character q acts on qubit q; one of I X Y Z, length
  * n) into a term.  Host only. */

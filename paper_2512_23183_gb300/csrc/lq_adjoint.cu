@@ -389,7 +389,7 @@ cudaError_t launch_pass2(const PassParams& P, double2* psi, double2* lam, double
   const int pgrid = (int)g < grid ? (int)g : grid;
   if (P.h.flags & PF_DYADIC) {
     cudaError_t e;
-    const double2* t = dyadic_tables(&e);
+    const double2* t = dyadic_tables(&e, &s);
     if (!t) return e;
     static thread_local PassParams Q;
     Q = P;

@@ -372,7 +372,7 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B,
       bp.h = S.passes[p].h;
       if (bp.h.flags & PF_DYADIC) {
         cudaError_t e;
-        bp.h.dtab = dyadic_tables(&e);
+        bp.h.dtab = dyadic_tables(&e, nullptr);
         if (!bp.h.dtab) return fail(LQ_ERR_CUDA, "dyadic tables: %s", cudaGetErrorString(e));
       }
       bp.op_first = (int)B.ops.size();

@@ -47,26 +47,68 @@ __global__ void dyadic_table_kernel() {
   g_dyadic[i] = make_double2(cs, sn);
 }
 
+// Constant device tables (the dyadic phase tables here, the FFT twiddles of
+// the QFT) are filled once per device before the first kernel that reads them
+// is enqueued.  The fill runs under a mutex on a private non-blocking stream
+// and only that stream is synchronised, so other streams keep running and a
+// caller's stream capture is not disturbed; the device is marked done only
+// after the fill has completed, so a launch enqueued on any stream after the
+// mark (or after another thread's fill returned) reads a finished table.  A
+// first fill requested from a stream that is being captured is refused, since
+// the caller would then record kernels that read a table this call has not
+// filled yet.
+cudaError_t fill_table_once(TableOnce& t, const cudaStream_t* caller,
+                            cudaError_t (*fill)(cudaStream_t)) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  const uint64_t bit = 1ull << dev;
+  if (t.done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  if (caller) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(*caller, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+  }
+  std::lock_guard<std::mutex> lock(t.mu);
+  if (t.done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  cudaStream_t ps = nullptr;
+  e = cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  e = fill(ps);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+  cudaStreamDestroy(ps);
+  if (e == cudaSuccess) t.done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
+
+static cudaError_t fill_dyadic(cudaStream_t ps) {
+  dyadic_table_kernel<<<(2u << DYADIC_HALF) / 256, 256, 0, ps>>>();
+  return cudaGetLastError();
+}
+
 // Device address of the tables of the current device, filling them on first
-// use (synchronously, so no stream can read them before they are complete).
-const double2* dyadic_tables(cudaError_t* err) {
-  static std::mutex mu;
-  static const double2* ptr[64] = {nullptr};
+// use (see fill_table_once).
+const double2* dyadic_tables(cudaError_t* err, const cudaStream_t* caller) {
+  static TableOnce once;
+  static std::atomic<const double2*> ptr[64];
   int dev = 0;
   *err = cudaGetDevice(&dev);
-  if (*err != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!ptr[dev]) {
-    void* p = nullptr;
-    *err = cudaGetSymbolAddress(&p, g_dyadic);
-    if (*err != cudaSuccess) return nullptr;
-    dyadic_table_kernel<<<(2u << DYADIC_HALF) / 256, 256>>>();
-    *err = cudaGetLastError();
-    if (*err == cudaSuccess) *err = cudaDeviceSynchronize();
-    if (*err != cudaSuccess) return nullptr;
-    ptr[dev] = (const double2*)p;
+  if (*err != cudaSuccess) return nullptr;
+  if (dev < 0 || dev >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
   }
-  return ptr[dev];
+  const double2* p = ptr[dev].load(std::memory_order_acquire);
+  if (p) return p;
+  *err = fill_table_once(once, caller, fill_dyadic);
+  if (*err != cudaSuccess) return nullptr;
+  void* a = nullptr;
+  *err = cudaGetSymbolAddress(&a, g_dyadic);
+  if (*err != cudaSuccess) return nullptr;
+  ptr[dev].store((const double2*)a, std::memory_order_release);
+  return (const double2*)a;
 }
 
 // ----------------------------------------------------------- tile passes
@@ -275,7 +317,7 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
   int grid = (int)(total < cap ? total : cap);
   if (P.h.flags & PF_DYADIC) {
     cudaError_t e;
-    const double2* t = dyadic_tables(&e);
+    const double2* t = dyadic_tables(&e, &s);
     if (!t) return e;
     static thread_local PassParams Q;   // launch copy carrying the table address
     Q = P;

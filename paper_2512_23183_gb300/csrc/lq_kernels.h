@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -50,6 +51,7 @@ constexpr int XP_MAX_GROUPS = 192;
 constexpr int XP_MAX_TERMS = 512;
 constexpr int XP_MAX_COEF = 384;
 constexpr int XP_TABLE_TERMS = 4;   // terms per table-mode group
+constexpr int XP_CLASS_TERMS = 128; // terms per class-mode group (longer lists are split)
 enum XGroupMode : int8_t { XG_DIAG = 0, XG_CLASS = 1, XG_TABLE = 2 };
 struct XTerm {
   double c;        // c_t (diagonal) or 2 c_t (pair terms)
@@ -147,7 +149,18 @@ cudaError_t once_per_device(std::atomic<uint64_t>& done, F set) {
 // --------------------------------------------------------------- launchers
 
 int sm_count();
-const double2* dyadic_tables(cudaError_t* err);
+
+// Once-per-device fill of a constant device table (lq_kernels.cu).
+struct TableOnce {
+  std::mutex mu;
+  std::atomic<uint64_t> done{0};
+};
+// Runs fill(private stream) once per device and waits for it; `caller`, when
+// not null, is the stream of the launch that needs the table: a first fill
+// while it is being captured returns cudaErrorStreamCaptureUnsupported.
+cudaError_t fill_table_once(TableOnce& t, const cudaStream_t* caller,
+                            cudaError_t (*fill)(cudaStream_t));
+const double2* dyadic_tables(cudaError_t* err, const cudaStream_t* caller);
 int expval_grid(int n);
 
 cudaError_t launch_init_basis(double2* amps, int n, uint64_t basis, cudaStream_t s);
@@ -163,7 +176,7 @@ cudaError_t launch_psr_grad(const double* E, int np, double* out, cudaStream_t s
 cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, double scale,
                             cudaStream_t s);
 cudaError_t launch_bitrev(double2* state, int n, cudaStream_t s);
-cudaError_t fft_tables_init(cudaStream_t s);
+cudaError_t fft_tables_init(cudaStream_t s);   // fills the twiddle table once per device
 cudaError_t launch_expval(const ExpParams& E, const double2* state, uint64_t stride,
                           int nstates, double* partial, double* out, int accumulate,
                           cudaStream_t s);

@@ -54,16 +54,17 @@ __global__ void fft_table_kernel() {
   g_tw[idx] = cot ? make_double2(s, c / s) : make_double2(c, -s / c);
 }
 
+static cudaError_t fill_fft_table(cudaStream_t ps) {
+  fft_table_kernel<<<(FFT_TABLE + 255) / 256, 256, 0, ps>>>();
+  return cudaGetLastError();
+}
+
+// The twiddle table is filled once per device and complete before this
+// returns (fill_table_once), whichever thread or stream asks first.
 cudaError_t fft_tables_init(cudaStream_t s) {
   (void)cudaGetLastError();  // report only this launcher's own errors
-  static int done_dev[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && done_dev[dev]) return cudaSuccess;
-  fft_table_kernel<<<(FFT_TABLE + 255) / 256, 256, 0, s>>>();
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && dev >= 0 && dev < 64) done_dev[dev] = 1;
-  return e;
+  static TableOnce once;
+  return fill_table_once(once, &s, fill_fft_table);
 }
 
 struct FftParams {
@@ -455,6 +456,10 @@ extern "C" lq_status lq_qft(void* amps, int n, int inverse, int method, void* sc
     return LQ_OK;
   }
   cudaError_t e = fft_tables_init(s);
+  if (e == cudaErrorStreamCaptureUnsupported)
+    return fail(LQ_ERR_CUDA, "fft tables: the first FFT-form QFT on a device fills its twiddle "
+                "table and is refused while the stream is capturing; make one uncaptured call "
+                "first");
   if (e != cudaSuccess) return fail(LQ_ERR_CUDA, "fft tables: %s", cudaGetErrorString(e));
   std::vector<int> bounds = fft_bounds(n);
   const double scale = std::ldexp(1.0, -n / 2) * ((n & 1) ? 0.70710678118654752440 : 1.0);
