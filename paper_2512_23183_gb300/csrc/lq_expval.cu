@@ -83,8 +83,13 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
     bool cls = pc64(kv.first) <= 3;
     for (int t : kv.second)
       if (terms[t].zmask & ~kv.first) cls = false;
-    if (cls) {
-      groups.push_back(HG{kv.first, kv.second, XG_CLASS});
+    if (cls) {   // class groups of the same mask add up: split long term lists
+      for (std::size_t a = 0; a < kv.second.size(); a += XP_CLASS_TERMS) {
+        HG g{kv.first, {}, XG_CLASS};
+        for (std::size_t b = a; b < kv.second.size() && b < a + XP_CLASS_TERMS; b++)
+          g.t.push_back(kv.second[b]);
+        groups.push_back(g);
+      }
     } else {
       for (std::size_t a = 0; a < kv.second.size(); a += XP_TABLE_TERMS) {
         HG g{kv.first, {}, XG_TABLE};
@@ -94,7 +99,19 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
       }
     }
   }
-  // passes: greedy, groups in ascending x
+  // a diagonal group too long for one plan goes to the untiled kernel
+  if ((int)diag.t.size() > XP_MAX_TERMS / 2) {
+    for (int t : diag.t) wide.push_back(terms[t]);
+    diag.t.clear();
+  }
+  // what a group takes of an XPlan's groups, terms and coefficients
+  auto coefs = [](const HG& G) {
+    return G.mode == XG_CLASS ? 1 << (pc64(G.x) - 1)
+                              : G.mode == XG_TABLE ? 1 << (int)G.t.size() : 0;
+  };
+  // passes: greedy, groups in ascending x, each pass within one XPlan's
+  // capacity (a small state's tile holds every mask, so the tile bits alone
+  // would put all groups into one pass)
   struct HP {
     uint64_t tile;
     std::vector<int> g;   // indices into groups; -1 = the diagonal group
@@ -105,16 +122,24 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
   if (!diag.t.empty()) passes.push_back(HP{low, {-1}});
   while (!pending.empty()) {
     HP P{low, {}};
+    int ng = 0, ntm = 0, nco = 0;
     if (passes.size() == 1 && passes[0].g.size() == 1 && passes[0].g[0] == -1) {
       P = passes[0];   // the diagonal group shares the first pass
       passes.clear();
+      ng = 1;
+      ntm = (int)diag.t.size();
     }
     std::vector<int> rest;
     for (int g : pending) {
       const uint64_t t = P.tile | groups[g].x;
-      if (pc64(t) <= k) {
+      const int tg = (int)groups[g].t.size(), cg = coefs(groups[g]);
+      if (pc64(t) <= k && ng + 1 <= XP_MAX_GROUPS && ntm + tg <= XP_MAX_TERMS &&
+          nco + cg <= XP_MAX_COEF) {
         P.tile = t;
         P.g.push_back(g);
+        ng++;
+        ntm += tg;
+        nco += cg;
       } else {
         rest.push_back(g);
       }

@@ -161,6 +161,25 @@ def test_expval_many_terms_chunked(lq):
     assert lq.expval_pauli_sum(dev(psi), n, []) == 0.0
 
 
+@pytest.mark.parametrize("n,masks,diag,dup", [(12, 240, 5, 0), (14, 400, 0, 0), (12, 20, 300, 0),
+                                              (13, 3, 10, 300)])
+def test_expval_tiled_beyond_one_plan(lq, n, masks, diag, dup):
+    # more X-mask groups, terms or coefficients than one tiled plan holds: a
+    # small state is one tile, so the passes are split by capacity; a long
+    # diagonal group and a long class group (the same XX term repeated) too
+    rng = np.random.default_rng(n + masks + diag)
+    terms = []
+    for m in rng.choice(np.arange(1, 1 << n), size=masks, replace=False):
+        s = ["XY"[rng.integers(2)] if (int(m) >> (n - 1 - q)) & 1 else "IZ"[rng.integers(2)]
+             for q in range(n)]
+        terms.append((float(rng.standard_normal()), "".join(s)))
+    terms += [(float(rng.standard_normal()),
+               "".join("Z" if rng.random() < 0.3 else "I" for _ in range(n))) for _ in range(diag)]
+    terms += [(float(rng.standard_normal()), "XX" + "I" * (n - 2)) for _ in range(dup)]
+    psi = W.gaussian_state(n, 60 + n)
+    assert close_e(lq.expval_pauli_sum(dev(psi), n, terms), oracle.expval(psi, n, terms))
+
+
 def _pauli(n, ops, c=1.0):
     """(c, string) with ops = {qubit: 'X'|'Y'|'Z'}."""
     s = ["I"] * n
@@ -271,16 +290,38 @@ def test_qft_gate_form_large_against_fft_form(lq, n):
     np.testing.assert_allclose(host(b), psi, rtol=0, atol=ATOL)
 
 
-@pytest.mark.parametrize("n", [22, 24])
+@pytest.mark.parametrize("n", [20, 22, 24, 28])
 def test_qft_basis_closed_form_sampled(lq, n):
+    # QFT|x> = N^{-1/2} sum_k e^{2 pi i x k / N}|k>, phase index x k mod N in
+    # integers; both forms, at the basis inputs of the QFT workload sizes
+    import torch
+
     N = 1 << n
     x = W.basis_index(n, 2000 + n)
-    t = lq.new_state(n, x)
-    lq.qft(t, n)
-    got = host(t)
     k = np.random.default_rng(n).integers(0, N, 4096)
     want = np.exp(2j * np.pi * ((x * k) % N) / N) / np.sqrt(N)
-    np.testing.assert_allclose(got[k], want, rtol=0, atol=ATOL)
+    for meth in (lq.QFT_FFT, lq.QFT_GATES):
+        t = lq.new_state(n, x)
+        lq.qft(t, n, method=meth)
+        got = t[torch.from_numpy(k).cuda()].cpu().numpy()
+        np.testing.assert_allclose(got, want, rtol=0, atol=ATOL)
+        del t
+
+
+def test_qft_n24_gaussian_both_forms_against_oracle(lq):
+    # the seeded Gaussian input of the QFT workload at n = 24, where the
+    # forward gate form uses its reordered list: both forms and both
+    # directions element-wise against the oracle's plain radix-2 inverse DFT
+    n = 24
+    psi = W.gaussian_state(n, 1000 + n)
+    want = {False: oracle.qft_fft(psi.copy(), n), True: oracle.qft_fft(psi.copy(), n, inverse=True)}
+    for meth in (lq.QFT_FFT, lq.QFT_GATES):
+        for inverse in (False, True):
+            t = dev(psi)
+            lq.qft(t, n, inverse=inverse, method=meth)
+            err = float(np.abs(host(t) - want[inverse]).max())
+            assert err < ATOL, (meth, inverse, err)
+            del t
 
 
 # ------------------------------------------------------------ gradients

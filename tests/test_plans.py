@@ -52,3 +52,23 @@ def test_inverse_gate_qft_default_schedule_n30():
     p = lq.qft_plan(n, lq.QFT_GATES, inverse=True)
     assert p["tile_bits"] == 10 and p["npasses"] == 5 + 1
     assert p["dram_bytes"] == 6 * 32 * 2.0 ** n
+
+
+@pytest.mark.parametrize("n,masks,diag", [(12, 240, 5), (14, 400, 0), (12, 20, 300)])
+def test_expval_plan_splits_passes_beyond_one_plan(n, masks, diag):
+    # a 2^12-amplitude state is one tile, so every X mask fits the first pass;
+    # the passes must still respect one plan's group/term/coefficient
+    # capacity (and a diagonal group of hundreds of terms goes to the untiled
+    # kernel) instead of failing
+    import numpy as np
+
+    rng = np.random.default_rng(n + masks)
+    terms = []
+    for m in rng.choice(np.arange(1, 1 << n), size=masks, replace=False):
+        s = ["XY"[rng.integers(2)] if (int(m) >> (n - 1 - q)) & 1 else "IZ"[rng.integers(2)]
+             for q in range(n)]
+        terms.append((float(rng.standard_normal()), "".join(s)))
+    terms += [(1.0, "".join("Z" if rng.random() < 0.3 else "I" for _ in range(n)))
+              for _ in range(diag)]
+    p = lq.expval_plan(n, terms)
+    assert p["npasses"] >= 2
