@@ -4,7 +4,8 @@ properties that hold at any size.
 
   - QFT n = 28 (Gaussian input: sampled amplitudes by the oracle's
     one-amplitude DFT) and n = 30 (basis input: closed form; Gaussian input:
-    inverse round trip, FFT form against gate form, norm);
+    sampled amplitudes of both forms by the oracle's one-amplitude DFT,
+    inverse round trip, norm);
   - VQE n = 10 depth 4, 80 angles seed 1: energy and full gradient;
   - batched PSR n = 16 depth 8 ring, 256 angles seed 3: energy by the oracle,
     sampled gradient entries by oracle energies at +-pi/2;
@@ -76,21 +77,51 @@ def test_qft_n30_basis_closed_form_and_properties(lq):
     del t
 
 
+def _device_gaussian(n, seed):
+    """The n-qubit seeded Gaussian input drawn on the device (i.i.d. N(0, 1)
+    real and imaginary parts from a seeded torch CUDA generator, then
+    L2-normalised), as the benchmark draws its 16 GiB input."""
+    import torch
+
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    v = torch.randn(2 << n, dtype=torch.float64, device="cuda", generator=g)
+    psi = torch.view_as_complex(v.view(-1, 2))
+    psi /= torch.linalg.vector_norm(psi)
+    return psi
+
+
+def test_qft_n30_gaussian_sampled_both_forms(lq):
+    # n = 30 Gaussian input: amplitudes of both forms (forward) against the
+    # oracle's one-amplitude DFT on a host copy of the same input
+    import torch
+
+    n = 30
+    psi = _device_gaussian(n, 1000 + n)
+    x = psi.cpu().numpy()
+    del psi
+    ks = [0, 1, 0x2AAAAAAB, (1 << n) - 1]
+    want = np.array([oracle.qft_amplitude(x, n, k) for k in ks])
+    idx = torch.tensor(ks, device="cuda")
+    for meth in (lq.QFT_FFT, lq.QFT_GATES):
+        t = torch.from_numpy(x).cuda()
+        lq.qft(t, n, method=meth)
+        got = t[idx].cpu().numpy()
+        del t
+        np.testing.assert_allclose(got, want, rtol=0, atol=ATOL, err_msg=str(meth))
+
+
 def test_qft_n30_gaussian_round_trip(lq):
     import torch
 
     n = 30
-    g = torch.Generator(device="cuda")
-    g.manual_seed(1000 + n)
-    v = torch.randn(2 << n, dtype=torch.float64, device="cuda", generator=g)
-    psi = torch.view_as_complex(v.view(-1, 2))
-    psi /= torch.linalg.vector_norm(psi)
+    psi = _device_gaussian(n, 1000 + n)
     ref = psi.clone()
     lq.qft(psi, n)
     assert abs(float(torch.linalg.vector_norm(psi)) - 1.0) < 1e-12
     lq.qft(psi, n, inverse=True, method=lq.QFT_GATES)
     assert float((psi - ref).abs().max()) < ATOL
-    del psi, ref, v
+    del psi, ref
 
 
 def test_vqe_n10_config_exact(lq):

@@ -84,10 +84,23 @@ def diagonal_run_circuit(n, rng, layers=3):
     return gates, p
 
 
-@pytest.mark.parametrize("n,seed", [(9, 5), (13, 6), (16, 7)])
+@pytest.mark.parametrize("n", [18, 20])
+def test_adjoint_wide_sweep_tiles_match_oracle(lq, n):
+    # from n = 18 the reverse sweep runs 2^11-amplitude tiles: every entry of
+    # the gradient against the oracle's parameter-shift rule
+    gates, P = W.hea(n, 2, "ladder")
+    th = W.angles(P, 60 + n)
+    terms = W.heisenberg(n)
+    e_w, g_w = oracle.param_shift(n, gates, th, terms)
+    e, g = lq.adjoint_grad(n, gates, th, terms)
+    assert abs(e - e_w) <= RTOL * max(1, abs(e_w))
+    np.testing.assert_allclose(g, g_w, rtol=0, atol=RTOL * max(1.0, np.abs(g_w).max()))
+
+
+@pytest.mark.parametrize("n,seed", [(9, 5), (13, 6), (16, 7), (18, 8)])
 def test_adjoint_diagonal_runs(lq, n, seed):
     rng = np.random.default_rng(seed)
-    gates, P = diagonal_run_circuit(n, rng, layers=3 if n < 16 else 2)
+    gates, P = diagonal_run_circuit(n, rng, layers=3 if n < 16 else 2 if n < 18 else 1)
     th = rng.uniform(-np.pi, np.pi, P)
     terms = W.random_pauli_sum(n, 20, rng, kmin=1, kmax=3)
     e_w, g_w = oracle.param_shift(n, gates, th, terms, general=True)
