@@ -40,8 +40,27 @@ if ROOT not in sys.path:
 
 METRIC = "state-vector HBM GB/s (% peak); VQE grads/s plain vs batched; serve p50/p99"
 UNIT = "GB/s"
-FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-FP64_MEASURED_TFLOPS = 1.19  # DFMA microbenchmark on the GB300s
+# nominal GB300 FP64 from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+# State passes of the step's rows (HEA layer, FFT-form QFT with its bit
+# reversal, inverse gate-form QFT with its bit reversal, <H> reads) under the
+# library's default (untuned) schedules, at the sizes the oracle sample runs:
+# the oracle arm counts its bytes with these, so it never loads the CUDA
+# library.  tests/test_bench_cpu.py checks them against the library's plans.
+ORACLE_STEP_PASSES = {10: (1, 2, 2, 10), 11: (2, 2, 3, 11), 12: (2, 2, 3, 1), 13: (2, 3, 3, 2),
+                      14: (2, 3, 3, 2), 15: (2, 3, 3, 2), 16: (3, 3, 4, 2), 17: (3, 3, 4, 2),
+                      18: (3, 3, 4, 2), 19: (3, 3, 4, 3), 20: (3, 3, 4, 3), 21: (4, 3, 5, 3),
+                      22: (4, 3, 5, 3), 23: (4, 4, 5, 3), 24: (4, 4, 5, 3)}
+
+
+def step_bytes(n, passes):
+    """Algorithmic state bytes of one step at n qubits: the copy-in (read and
+    write), 32 B per amplitude per tile pass, 16 B per amplitude per
+    read-only <H> pass."""
+    N = float(1 << n)
+    hea, fft, gates, reads = passes
+    return 32 * N * (1 + hea + fft + gates) + 16 * N * reads
 
 
 def parse():
@@ -56,6 +75,8 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=23, help="qubits of the bounded oracle sample")
     ap.add_argument("--cpu-s", type=float, default=10.0,
                     help="seconds of CPU work the oracle sample spans at least")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="requests of the serving measurement (Poisson pass)")
     return ap.parse_args()
 
 
@@ -142,6 +163,28 @@ def measured_peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def fp64_roof(gpu_index, reps=30):
+    """The FP64 roof of this GPU, measured in set-up: the library's DFMA
+    throughput probe (independent FMA chains, every SM filled; best of
+    `reps` launches timed with CUDA events) with nvidia-smi clocks sampled
+    meanwhile."""
+    import paper_2512_23183_gb300 as lq
+
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    t0 = time.perf_counter()
+    tf, ms = 0.0, 0.0
+    while time.perf_counter() - t0 < 0.6:   # long enough for a few clock samples
+        t, m = lq.measure_fp64_fma(reps=reps)
+        if t > tf:
+            tf, ms = t, m
+    clk = clocks.stop()
+    return {"tflops": round(tf, 4), "ms_per_launch": round(ms, 3),
+            "nominal_tflops": round(FP64_NOMINAL_TFLOPS, 4), "clocks": clk,
+            "how": "lq_measure_fp64_fma: 8 independent DFMA chains per thread, 4096 FMAs each, "
+                   "every SM filled, best launch by CUDA events"}
 
 
 def profiled_traffic(kernel):
@@ -294,6 +337,9 @@ def bench_lq(a, rank, world, device):
 
     lq.load()
     step = Step(a.n, device)
+    gpu_index = torch.cuda.current_device() if world == 1 else int(os.environ.get("LOCAL_RANK", 0))
+    roof = fp64_roof(gpu_index)
+    fp64_peak = roof["tflops"]
     for _ in range(a.warmup):
         step.run()
     torch.cuda.synchronize()
@@ -302,7 +348,7 @@ def bench_lq(a, rank, world, device):
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(a.steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(torch.cuda.current_device() if world == 1 else int(os.environ.get("LOCAL_RANK", 0)))
+    clocks = ClockSampler(gpu_index)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -332,8 +378,10 @@ def bench_lq(a, rank, world, device):
     for nm in names:
         r = step.rows[nm]
         t = seg_ms[nm] / a.steps
+        tf = r["flops"] / (t * 1e-3) / 1e12 if t else None
         rows[nm] = dict(ms=round(t, 3), gbs=round(r["bytes"] / (t * 1e-3) / 1e9, 1) if t else None,
-                        fp64_tflops=round(r["flops"] / (t * 1e-3) / 1e12, 4) if t else None,
+                        fp64_tflops=round(tf, 4) if t else None,
+                        fp64_frac=round(tf / fp64_peak, 4) if t else None,
                         launches=r["launches"])
     # dominant kernel: the kernel family with the largest share of the step
     fam = {}
@@ -352,11 +400,13 @@ def bench_lq(a, rank, world, device):
     bytes_pl = f["bytes"] / max(f["launches"], 1)
     ach_tf = flops_pl / per_launch_s / 1e12
     ach_gbs = bytes_pl / per_launch_s / 1e9
-    roofline = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(ach_tf / FP64_PEAK_TFLOPS, 4),
+    roofline = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": round(ach_tf / fp64_peak, 4),
                 "traffic": profiled_traffic(dom), "kernel": dom,
-                "peak_note": "FP64 nominal (recipe); DFMA microbenchmark measured %.2f"
-                             % FP64_MEASURED_TFLOPS,
+                "peak_note": "measured on this GPU in set-up (DFMA probe, fp64_roof); nominal "
+                             "%.3f TFLOP/s from 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz, frac "
+                             "of nominal %.4f" % (FP64_NOMINAL_TFLOPS, ach_tf / FP64_NOMINAL_TFLOPS),
+                "peak_nominal": round(FP64_NOMINAL_TFLOPS, 4),
                 "flops_note": "achieved counts the plans' flops (FMA = 2, add/multiply = 1); "
                               "a DADD or DMUL takes an FP64 issue slot like a DFMA, so the "
                               "FP64-pipe activity ncu measures is higher: 83-85% on the HEA "
@@ -386,6 +436,7 @@ def bench_lq(a, rank, world, device):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "hbm_frac": round(value / hbm_peak, 4),
         "rows": rows, "kernels": kernels, "roofline": roofline,
+        "fp64_roof": roof,
         "autotune_hea_layer": step.tune,
         "autotune_qft_gates_inverse": step.tune_qft,
         "gpu_launches": launches * a.steps,
@@ -564,7 +615,7 @@ def next_rows_extras(device):
     return out
 
 
-def qft_extras(device, sizes=(20, 24, 28, 30), reps=3):
+def qft_extras(device, fp64_peak, sizes=(20, 24, 28, 30), reps=3):
     """The QFT workload as configured: FFT form and gate form at n = 20, 24,
     28, 30 on seeded Gaussian inputs, each timed with CUDA events (mean of
     `reps` after a warm-up): ms, state-vector GB/s by the plan's algorithmic
@@ -598,7 +649,7 @@ def qft_extras(device, sizes=(20, 24, 28, 30), reps=3):
             gbs = plan["dram_bytes"] / (ms * 1e-3) / 1e9
             tf = plan["dp_flops"] / (ms * 1e-3) / 1e12
             r[name] = {"ms": round(ms, 3), "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4),
-                       "fp64_tflops": round(tf, 4), "fp64_frac": round(tf / FP64_PEAK_TFLOPS, 4),
+                       "fp64_tflops": round(tf, 4), "fp64_frac": round(tf / fp64_peak, 4),
                        "launches": plan["npasses"]}
         out["n%d" % n] = r
         del psi, v
@@ -606,13 +657,14 @@ def qft_extras(device, sizes=(20, 24, 28, 30), reps=3):
     return out
 
 
-def serve_extras(device, count=48, slots=8):
+def serve_extras(device, count=48, slots=8, closed=48):
     """Serving workload: seeded request stream (n ~ U{8..28}, depth ~
     U{2..20}, 50/50 energy / energy+gradient, Heisenberg chain or random
     50-term sums), admitted by footprint against a device arena of up to
-    150 GB.  A closed-loop pass measures capacity; then the same requests
-    arrive as a Poisson stream at 70% of it.  Reports throughput and p50/p99
-    latency (submit -> done)."""
+    150 GB.  A closed-loop pass over the first `closed` requests measures
+    capacity; then `count` requests arrive as a Poisson stream at 70% of it.
+    Reports throughput, p50/p99 latency (submit -> done) with the number of
+    samples behind them, and how many requests were in flight together."""
     import numpy as np
     import torch
 
@@ -623,13 +675,15 @@ def serve_extras(device, count=48, slots=8):
     budget = int(min(150e9, free - 8e9))
     arena = torch.empty(budget, dtype=torch.uint8, device=device)
     reqs = W.serve_requests(count, seed=6)
+    closed = min(closed, count)
     srv = lq.Server(arena, slots=slots)
     try:
         t0 = time.perf_counter()
-        ids = [srv.submit(r["n"], r["gates"], r["params"], r["terms"], r["grad"]) for r in reqs]
+        ids = [srv.submit(r["n"], r["gates"], r["params"], r["terms"], r["grad"])
+               for r in reqs[:closed]]
         for i in ids:
             srv.result(i)
-        cap = count / (time.perf_counter() - t0)
+        cap = closed / (time.perf_counter() - t0)
         rate = 0.7 * cap
         gaps = np.random.default_rng(6).exponential(1.0 / rate, count)
         arrivals = np.cumsum(gaps)
@@ -644,14 +698,26 @@ def serve_extras(device, count=48, slots=8):
         end = max(t[2] for _, _, t in res)
         first = min(t[0] for _, _, t in res)
         lat = np.array([t[2] - t[0] for _, _, t in res])
+        # requests in flight together: the largest number of overlapping
+        # [t_start, t_done] intervals (one stream per slot)
+        ev = sorted([(t[1], 1) for _, _, t in res] + [(t[2], -1) for _, _, t in res])
+        cur = peak = 0
+        for _, d in ev:
+            cur += d
+            peak = max(peak, cur)
     finally:
         srv.close()
         del arena
     return {"requests": count, "slots": slots, "arena_gb": round(budget / 1e9, 1),
+            "closed_loop_requests": closed,
             "closed_loop_req_per_s": round(cap, 3), "poisson_rate_req_per_s": round(rate, 3),
             "throughput_req_per_s": round(count / (end - first), 3),
             "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 2),
             "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2),
+            "latency_samples": int(lat.size),
+            "p99_note": "p99 of %d samples%s" % (lat.size, " (= the largest latency)"
+                                                 if lat.size < 100 else ""),
+            "max_in_flight": peak,
             "workload": "seed 6: n~U{8..28}, depth~U{2..20}, 50/50 energy/grad (adjoint), "
                         "Heisenberg chain or random 50-term"}
 
@@ -678,11 +744,10 @@ def oracle_sample_rate(n):
     oracle.qft_gates(work, n)                            # a6 (forward gate form, same cost)
     e = oracle.expval(work, n, terms)                    # a7
     dt = time.perf_counter() - t0
-    import paper_2512_23183_gb300 as lq                  # plan only (host): byte accounting
-
-    N = float(1 << n)
-    byts = (32 * N + lq.circuit_plan(n, layer, th)["dram_bytes"] + lq.qft_plan(n, 0)["dram_bytes"]
-            + lq.qft_plan(n, 1)["dram_bytes"] + lq.expval_plan(n, terms)["dram_bytes"])
+    if n not in ORACLE_STEP_PASSES:
+        raise SystemExit("no pass counts for an oracle sample at n=%d (have %s)"
+                         % (n, sorted(ORACLE_STEP_PASSES)))
+    byts = step_bytes(n, ORACLE_STEP_PASSES[n])
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     del e, np
     return byts / dt / 1e9, dt, threads
@@ -700,7 +765,8 @@ def cpu_baseline(n, min_s):
     return {"value": round(byts / total / 1e9, 3), "unit": UNIT, "cores": threads,
             "kind": "oracle",
             "sample": "%d step(s) (a1-a7) at n=%d (%.1f s of CPU work; a8/a9 excluded), "
-                      "same algorithmic-bytes formula" % (steps, n, total)}
+                      "same algorithmic-bytes formula; a rate at n=%d, not the GPU's size"
+                      % (steps, n, total, n)}
 
 
 def run_reference(a, rank, world):
@@ -721,7 +787,9 @@ def run_reference(a, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "sv_step_n%d" % a.n,
-                       "sample": "oracle step a1-a7 at n=%d per step" % n},
+                       "sample": "oracle step a1-a7 at n=%d per step (a rate comparison at a "
+                                 "different n: the oracle's whole step at n=%d would take hours)"
+                                 % (n, a.n)},
             "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": threads,
                              "kind": "oracle", "sample": "step a1-a7 at n=%d" % n},
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -749,12 +817,12 @@ def main():
     torch.cuda.empty_cache()
     if rank == 0:
         if not a.no_extras:
-            out["qft"] = qft_extras(device)
+            out["qft"] = qft_extras(device, out["fp64_roof"]["tflops"])
             out["vqe"] = vqe_extras(device)
             torch.cuda.empty_cache()
             out["next_rows"] = next_rows_extras(device)
             torch.cuda.empty_cache()
-            out["serve"] = serve_extras(device)
+            out["serve"] = serve_extras(device, count=a.serve_requests)
         out["cpu_baseline"] = cpu_baseline(a.cpu_n, a.cpu_s)
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -74,6 +74,7 @@ class LqResult(ctypes.Structure):
 KINDS = {name: i for i, name in enumerate(
     "H X Y Z S SDG T TDG RX RY RZ P U1 CNOT CY CZ CP SWAP CRX CRY CRZ RXX RYY RZZ CCX U2".split())}
 
+LQ_ERR_TIMEOUT = 6
 STATUS = {0: "LQ_OK", 1: "LQ_ERR_INVALID_ARG", 2: "LQ_ERR_UNSUPPORTED", 3: "LQ_ERR_NONFINITE",
           4: "LQ_ERR_OOM", 5: "LQ_ERR_CUDA", 6: "LQ_ERR_TIMEOUT"}
 PSR_PLAIN, PSR_BATCHED = 0, 1
@@ -99,7 +100,7 @@ EXPORTS = [
     "lq_server_submit", "lq_server_wait", "lq_server_destroy", "lq_vqe_workspace_size",
     "lq_vqe_adam", "lq_adjoint_plan", "lq_expval_plan", "lq_autotune_circuit",
     "lq_tune_cache_save", "lq_tune_cache_load", "lq_tune_cache_clear", "lq_tune_cache_size",
-    "lq_autotune_batch", "lq_autotune_param_shift", "lq_autotune_qft",
+    "lq_autotune_batch", "lq_autotune_param_shift", "lq_autotune_qft", "lq_measure_fp64_fma",
 ]
 
 
@@ -182,6 +183,7 @@ def load(build_if_missing=True):
     L.lq_tune_cache_clear.argtypes = []
     L.lq_tune_cache_size.argtypes = []
     L.lq_tune_cache_size.restype = ctypes.c_int
+    L.lq_measure_fp64_fma.argtypes = [ctypes.c_int, P(c_double), P(c_double), c_void_p]
     L.lq_adjoint_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
                                   ctypes.c_int, P(LqPlanInfo)]
     _lib = L
@@ -198,6 +200,15 @@ def _check(st):
 
 def version():
     return load().lq_version().decode()
+
+
+def measure_fp64_fma(reps=5, stream=None):
+    """Measured FP64 FMA rate of the current device: (TFLOP/s, ms of the best
+    launch)."""
+    tf, ms = c_double(), c_double()
+    _check(load().lq_measure_fp64_fma(int(reps), ctypes.byref(tf), ctypes.byref(ms),
+                                      _stream(stream)))
+    return tf.value, ms.value
 
 
 # ------------------------------------------------------------- marshalling
@@ -614,11 +625,16 @@ class Server:
         return rid.value
 
     def result(self, rid, timeout=600.0):
-        np_, want_grad = self._np.pop(rid)
+        """Waits up to `timeout` seconds; LqError with LQ_ERR_TIMEOUT when the
+        request is not done by then (it stays queued: wait again later)."""
+        np_, want_grad = self._np[rid]
         res = LqResult()
         grad = np.zeros(max(np_, 1))
-        _check(load().lq_server_wait(self.h, rid, float(timeout), ctypes.byref(res),
-                                     grad.ctypes.data_as(ctypes.POINTER(c_double))))
+        st = load().lq_server_wait(self.h, rid, float(timeout), ctypes.byref(res),
+                                   grad.ctypes.data_as(ctypes.POINTER(c_double)))
+        if st != LQ_ERR_TIMEOUT:
+            del self._np[rid]
+        _check(st)
         return res.energy, (grad[:np_].copy() if want_grad else None), (res.t_submit, res.t_start,
                                                                        res.t_done)
 

@@ -80,3 +80,40 @@ def test_reference_arm_two_ranks_prints_once():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _json_lines(r.stdout)
     assert len(lines) == 1 and lines[0]["n_gpus"] == 2
+
+
+def test_oracle_arm_pass_table_matches_library_plans():
+    # the oracle arm counts its bytes from a pass table so that it never loads
+    # the CUDA library; the table must be the library's own default schedules
+    sys.path.insert(0, ROOT)
+    import bench
+    import paper_2512_23183_gb300 as lq
+    import workloads as W
+
+    lq.tune_cache_clear()
+    for n, passes in bench.ORACLE_STEP_PASSES.items():
+        layer, P = W.hea(n, 1, "ladder")
+        th = W.angles(P, 2000 + n)
+        N = 2.0 ** n
+        got = (lq.circuit_plan(n, layer, th)["dram_bytes"] / (32 * N),
+               lq.qft_plan(n, lq.QFT_FFT)["dram_bytes"] / (32 * N),
+               lq.qft_plan(n, lq.QFT_GATES, inverse=True)["dram_bytes"] / (32 * N),
+               lq.expval_plan(n, W.heisenberg(n))["dram_bytes"] / (16 * N))
+        assert got == passes, n
+        want = (32 * N + lq.circuit_plan(n, layer, th)["dram_bytes"]
+                + lq.qft_plan(n, lq.QFT_FFT)["dram_bytes"]
+                + lq.qft_plan(n, lq.QFT_GATES, inverse=True)["dram_bytes"]
+                + lq.expval_plan(n, W.heisenberg(n))["dram_bytes"])
+        assert bench.step_bytes(n, passes) == want
+
+
+def test_reference_arm_loads_no_product_library():
+    # the reference arm runs the oracle only: the CUDA library is not mapped
+    code = ("import sys, runpy; sys.argv = ['bench.py', '--impl', 'reference', '--steps', '1', "
+            "'--warmup', '0', '--cpu-n', '12']; runpy.run_path('bench.py', run_name='__main__'); "
+            "maps = open('/proc/self/maps').read(); "
+            "assert 'liblq.so' not in maps, 'liblq.so mapped'; "
+            "assert 'liblq_oracle.so' in maps; print('maps ok')")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and "maps ok" in r.stdout, r.stdout + r.stderr
