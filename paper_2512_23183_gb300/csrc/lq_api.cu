@@ -188,6 +188,7 @@ static lq_status run_ops(double2* states, uint64_t stride, int nstates, int n, c
   opt.lphase_table = true;   // run by pass_kernel
   if (tuned) opt = *tuned;
   opt.max_hi = PASS_HI_BITS;
+  opt.sink_phases = true;
   Schedule S;
   lq_status st = schedule_ops(n, ops, nops, zr, zi, opt, S);
   if (st) return st;
@@ -328,6 +329,7 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
   opt.lphase_table = true;   // run by pass_kernel
   tuned_options(n, gates, ng, &opt);   // the schedule lq_apply_circuit would use
   opt.max_hi = PASS_HI_BITS;
+  opt.sink_phases = true;
   Schedule S;
   st = schedule_ops(n, ops, nops, zr, zi, opt, S);
   delete[] ops;

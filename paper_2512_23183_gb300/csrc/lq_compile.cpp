@@ -6,6 +6,7 @@
 // exp(-i theta sigma/2), Sec. III-A; CNOT and Toffoli as the bit-mask swaps of
 // Alg. 1 and Alg. 4; CP as diag(1,1,1,e^{i theta}), Alg. 3) with qubit q at bit
 // n-1-q of the amplitude index (MSB-first).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -308,7 +309,7 @@ static bool one_bit_phase(const LOp& o, bool params) {
 }
 
 static void phase_value(const LOp& o, double* a, double* b) {
-  if (o.type == OP_PHASE) {
+  if (o.type == OP_PHASE || o.type == OP_PARITY) {
     *a = o.a;
     *b = o.b;
   } else if (o.type == OP_SIGN) {
@@ -321,25 +322,37 @@ static void phase_value(const LOp& o, double* a, double* b) {
   }
 }
 
+// A parity phase (w on the amplitudes with odd popcount(idx & z)) with at
+// most one of its bits in the pass's tile: a factor of a merged one-bit phase
+// op, its other bits giving a per-tile constant.
+static bool tile_parity_phase(const LOp& o, bool params, uint64_t tile) {
+  if (!tile || o.type != OP_PARITY || o.cm != 0 || o.z == 0) return false;
+  if (!params && !o.fixed) return false;
+  return popc64(o.z & tile) <= 1;
+}
+
 void merge_linear(std::vector<LOp>& ops, int n, bool params, std::vector<int>* src,
-                  int coef_budget) {
+                  int coef_budget, uint64_t tile) {
   std::vector<LOp> out;
   std::vector<int> osrc;
   out.reserve(ops.size());
+  auto mergeable = [&](const LOp& o) {
+    return one_bit_phase(o, params) || tile_parity_phase(o, params, tile);
+  };
   std::size_t i = 0;
   while (i < ops.size()) {
-    if (!one_bit_phase(ops[i], params)) {
+    if (!mergeable(ops[i])) {
       if (src) osrc.push_back((*src)[i]);
       out.push_back(ops[i++]);
       continue;
     }
     std::size_t j = i;
-    while (j < ops.size() && one_bit_phase(ops[j], params)) j++;
+    while (j < ops.size() && mergeable(ops[j])) j++;
     double separate = 0;
     uint64_t all = 0;
     for (std::size_t k = i; k < j; k++) {
       separate += op_flops(ops[k], n);
-      all |= ops[k].cm;
+      all |= ops[k].cm | (ops[k].type == OP_PARITY ? ops[k].z : 0);
     }
     LOp m;
     m.type = OP_LPHASE;
@@ -353,8 +366,13 @@ void merge_linear(std::vector<LOp>& ops, int n, bool params, std::vector<int>* s
     for (std::size_t k = i; k < j; k++) {
       double a, b;
       phase_value(ops[k], &a, &b);
-      m.dfac.push_back(ops[k].cm);
-      m.dfac.push_back(ops[k].cv);
+      if (ops[k].type == OP_PARITY) {   // condition: odd parity of idx & z
+        m.dfac.push_back(ops[k].z);
+        m.dfac.push_back(ops[k].z | kLphaseParity);
+      } else {
+        m.dfac.push_back(ops[k].cm);
+        m.dfac.push_back(ops[k].cv);
+      }
       m.dfac.push_back(dbits_u(a));
       m.dfac.push_back(dbits_u(b));
       m.dfac.push_back((uint64_t)(int64_t)ops[k].gate);   // for per-circuit patches
@@ -545,6 +563,176 @@ static void fill_op(Op& d, const LOp& s, uint64_t tile, const int* pos, int coef
   d.b = s.b;
 }
 
+// ------------------------------------------------------------ phase sinking
+//
+// A one-bit phase (RZ, P, T on one qubit: the amplitudes with bit b set
+// times w) is diagonal, so it commutes with every op that does not mix bit b.
+// Moved past a CNOT-type permutation (X on target t under one control c,
+// y -> y ^ (y_c ? 2^t : 0)) it becomes a parity phase, w on the amplitudes
+// with odd popcount(y & M), where M gains or loses c when t is in M; a swap
+// exchanges the two bits of M.  So a hardware-efficient layer's RZ factors
+// need not be applied in every pass that holds some of them: moved forward
+// to the last pass they are parities of CTA bits there (per-tile constants)
+// or one-bit phases on its tile bits, and one merged phase op serves them
+// all.
+
+// A phase op that sinking may move: OP_PHASE on the amplitudes with one bit set.
+static bool sinkable_phase(const LOp& o) {
+  return o.type == OP_PHASE && o.cm != 0 && (o.cm & (o.cm - 1)) == 0 && o.cv == o.cm;
+}
+
+// Moves a parity phase with mask M from before op o to after it: false when
+// o mixes a bit of M other than as a CNOT-type target or a swap.
+static bool sink_past(const LOp& o, uint64_t& M) {
+  const uint64_t mx = o.mix();
+  if ((mx & M) == 0) return true;   // diagonal, or acts on other bits
+  if (o.type == OP_PAULI && (o.mode & 3) == PM_PERM && (mx & (mx - 1)) == 0 && o.cm != 0 &&
+      (o.cm & (o.cm - 1)) == 0 && o.cv == o.cm && (o.cm & mx) == 0) {
+    M ^= o.cm;   // CNOT, CY: parity(y' & M) = parity(y & (M ^ c)) for t in M
+    return true;
+  }
+  if (o.type == OP_SWAP) {
+    const uint64_t a = 1ull << o.g0, b = 1ull << o.g1;
+    if (((M & a) != 0) != ((M & b) != 0)) M ^= a | b;
+    return true;
+  }
+  return false;
+}
+
+// plists: the passes' ops in execution order (tiles: their tile bits).  Each
+// one-bit phase moves forward until an op mixes one of its bits; a point on
+// the way is usable when at most one bit of its mask there is a tile bit of
+// that point's pass.  Points are fixed greedily: the phase whose last usable
+// point comes first fixes a point there, and every phase usable at it joins
+// it.  The phases are re-inserted at their points (one-bit masks as OP_PHASE,
+// wider ones as OP_PARITY) when that leaves fewer points than passes with
+// phases; otherwise nothing changes.  A point is (pass, position in the
+// pass's list): before the op at that position, or at the end of the pass;
+// the phases themselves are diagonal and commute, so a moving phase skips
+// the others.
+static void sink_phases(const std::vector<uint64_t>& tiles, std::vector<std::vector<LOp>>& plists,
+                        std::vector<std::vector<int>>& psrcs) {
+  const int P = (int)plists.size();
+  if (P < 2) return;
+  struct Fac {
+    int p, q;        // the phase op: plists[p][q]
+    int first, cnt;  // its usable points in `pts`
+  };
+  struct Pt {
+    int key;         // off[p] + position
+    uint64_t M;
+  };
+  std::vector<int> off(P + 1, 0);
+  std::vector<Fac> facs;
+  int before = 0;
+  for (int p = 0; p < P; p++) {
+    off[p + 1] = off[p] + (int)plists[p].size() + 1;
+    bool any = false;
+    for (int q = 0; q < (int)plists[p].size(); q++)
+      if (sinkable_phase(plists[p][q])) {
+        facs.push_back(Fac{p, q, 0, 0});
+        any = true;
+      }
+    before += any;
+  }
+  if (before < 2) return;
+  std::vector<Pt> pts;
+  pts.reserve(facs.size() * 16);
+  for (Fac& f : facs) {
+    uint64_t M = plists[f.p][f.q].cm;
+    int p = f.p, q = f.q + 1;
+    f.first = (int)pts.size();
+    for (;;) {
+      if (popc64(M & tiles[p]) <= 1) pts.push_back(Pt{off[p] + q, M});
+      if (q == (int)plists[p].size()) {
+        if (p + 1 == P) break;
+        p++;
+        q = 0;
+        continue;
+      }
+      const LOp& o = plists[p][q];
+      if (!sinkable_phase(o) && !sink_past(o, M)) break;
+      q++;
+    }
+    f.cnt = (int)pts.size() - f.first;
+  }
+  // greedy points
+  std::vector<int> at(facs.size(), -1);
+  std::vector<uint64_t> mask(facs.size(), 0);
+  std::size_t left = facs.size();
+  int npoints = 0;
+  while (left && npoints < before) {
+    int x = 1 << 30;
+    for (std::size_t f = 0; f < facs.size(); f++)
+      if (at[f] < 0) x = std::min(x, pts[(std::size_t)(facs[f].first + facs[f].cnt - 1)].key);
+    npoints++;
+    for (std::size_t f = 0; f < facs.size(); f++) {
+      if (at[f] >= 0) continue;
+      const Pt* b = pts.data() + facs[f].first;
+      const Pt* e = b + facs[f].cnt;
+      const Pt* it = std::lower_bound(b, e, x, [](const Pt& a, int v) { return a.key < v; });
+      if (it != e && it->key == x) {
+        at[f] = x;
+        mask[f] = it->M;
+        left--;
+      }
+    }
+  }
+  if (left || npoints >= before) return;
+  // rebuild the passes that lose or gain phases
+  std::vector<int> order(facs.size());
+  for (std::size_t f = 0; f < facs.size(); f++) order[f] = (int)f;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return at[a] != at[b] ? at[a] < at[b] : a < b;
+  });
+  // the phase ops themselves (their passes' lists are rebuilt below)
+  std::vector<LOp> fop;
+  std::vector<int> fsrc;
+  fop.reserve(facs.size());
+  for (const Fac& f : facs) {
+    fop.push_back(plists[f.p][f.q]);
+    fsrc.push_back(psrcs[f.p][f.q]);
+  }
+  std::vector<char> touched(P, 0);
+  for (const Fac& f : facs) touched[f.p] = 1;
+  for (std::size_t f = 0; f < facs.size(); f++) {
+    const int p = (int)(std::upper_bound(off.begin(), off.end(), at[f]) - off.begin()) - 1;
+    touched[p] = 1;
+  }
+  std::size_t next = 0;   // into order, by point
+  for (int p = 0; p < P; p++) {
+    if (!touched[p]) continue;
+    std::vector<LOp> out;
+    std::vector<int> osrc;
+    out.reserve(plists[p].size() + 8);
+    osrc.reserve(plists[p].size() + 8);
+    while (next < order.size() && at[order[next]] < off[p]) next++;
+    for (int q = 0; q <= (int)plists[p].size(); q++) {
+      for (; next < order.size() && at[order[next]] == off[p] + q; next++) {
+        LOp o = fop[(std::size_t)order[next]];
+        const uint64_t M = mask[order[next]];
+        if ((M & (M - 1)) == 0) {
+          osrc.push_back(M == o.cm ? fsrc[(std::size_t)order[next]] : -1);
+          o.cm = o.cv = M;
+        } else {
+          o.type = OP_PARITY;
+          o.cm = o.cv = 0;
+          o.z = M;
+          o.dy = -1;
+          osrc.push_back(-1);
+        }
+        out.push_back(std::move(o));
+      }
+      if (q < (int)plists[p].size() && !sinkable_phase(plists[p][q])) {
+        out.push_back(plists[p][q]);
+        osrc.push_back(psrcs[p][q]);
+      }
+    }
+    plists[p].swap(out);
+    psrcs[p].swap(osrc);
+  }
+}
+
 lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, double zi,
                        const ScheduleOptions& opt, Schedule& out) {
   const int k = opt.k < n ? opt.k : n;
@@ -606,22 +794,53 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
   out.passes = new PassParams[passes.size() > 0 ? passes.size() : 1];
   out.pass_ops.clear();
   out.op_src = new int[(passes.size() > 0 ? passes.size() : 1) * MAX_OPS];
+  // the passes' ops in order, tiles filled up to k bits with the lowest
+  // unused bits (larger contiguous loads, fewer tiles)
+  std::vector<uint64_t> tiles(passes.size());
+  std::vector<std::vector<LOp>> plists(passes.size());
+  std::vector<std::vector<int>> psrcs(passes.size());
   for (std::size_t p = 0; p < passes.size(); p++) {
     Built& B = passes[p];
-    // fill the tile up to k bits with the lowest unused bits (larger
-    // contiguous loads, fewer tiles)
     for (int bit = 0; bit < n && popc64(B.tile) < k; bit++) B.tile |= 1ull << bit;
-    // the pass's ops in order; runs of one-bit phases merge within the pass
-    std::vector<LOp> plist;
-    std::vector<int> psrc;
+    tiles[p] = B.tile;
     for (int idx : B.idx) {
-      plist.push_back(ops[idx]);
-      psrc.push_back(idx);
+      plists[p].push_back(ops[idx]);
+      psrcs[p].push_back(idx);
     }
+  }
+  // the moved phases save FP64 work in proportion to the state, the search
+  // costs host time in proportion to the circuit: from 2^18 amplitudes on
+  // the first outweighs the second (at n = 16 they were about equal)
+  const bool sink = opt.sink_phases && n >= opt.sink_min_qubits;
+  if (sink) sink_phases(tiles, plists, psrcs);
+  for (std::size_t p = 0; p < passes.size(); p++) {
+    Built& B = passes[p];
+    // runs of one-bit (and, in the pass's tile, parity) phases merge within
+    // the pass
+    std::vector<LOp>& plist = plists[p];
+    std::vector<int>& psrc = psrcs[p];
     {
       int used = 0;
       for (const LOp& l : plist) used += l.ncoef;
-      merge_linear(plist, n, opt.merge_params, &psrc, MAX_COEF - used);
+      merge_linear(plist, n, opt.merge_params, &psrc, MAX_COEF - used, sink ? B.tile : 0);
+    }
+    // the circuit's final scalar as an unconditional factor of a merged
+    // phase op of the last pass instead of a separate scale op
+    bool folded = false;
+    if (sink && !opt.force_scale && p + 1 == passes.size() && need_scale) {
+      int used = 0;
+      for (const LOp& l : plist) used += l.ncoef;
+      for (LOp& l : plist) {
+        if (l.type != OP_LPHASE || used + LPHASE_FAC > MAX_COEF) continue;
+        l.dfac.push_back(0);
+        l.dfac.push_back(0);
+        l.dfac.push_back(dbits_u(zr));
+        l.dfac.push_back(dbits_u(zi));
+        l.dfac.push_back((uint64_t)(int64_t)-1);
+        l.ncoef += LPHASE_FAC;
+        folded = true;
+        break;
+      }
     }
     PassParams& P = out.passes[p];
     std::memset(&P.h, 0, sizeof P.h);
@@ -792,7 +1011,7 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
         }
       }
     }
-    if (p + 1 == passes.size() && need_scale) {
+    if (p + 1 == passes.size() && need_scale && !folded) {
       LOp s;
       s.type = OP_SCALE;
       s.mode = (uint8_t)((zi == 0.0 ? 1 : 0) | 2);
@@ -804,7 +1023,7 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
       cnt++;
     }
     P.h.nops = cnt;
-    out.pass_ops.push_back(std::move(plist));
+    out.pass_ops.push_back(plist);
   }
   return LQ_OK;
 }

@@ -830,8 +830,20 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
           const uint64_t loc = (uint64_t)__double_as_longlong(Ff[0]);
           const uint64_t gm = (uint64_t)__double_as_longlong(Ff[1]);
           const uint64_t gv = (uint64_t)__double_as_longlong(Ff[2]);
-          if ((base & gm) != gv) continue;
-          const uint32_t lm = (uint32_t)loc, lv = (uint32_t)(loc >> 32);
+          const uint32_t lm = (uint32_t)loc;
+          uint32_t lv = (uint32_t)(loc >> 32);
+          if (gv & kLphaseParity) {
+            // parity factor: w where popcount(idx & mask) is odd, i.e. where
+            // the tile bit (if any) differs from the parity of the CTA bits
+            const uint32_t pg = (uint32_t)__popcll(base & gm) & 1u;
+            if (lm == 0) {
+              if (!pg) continue;
+            } else {
+              lv = pg ? 0u : lm;
+            }
+          } else if ((base & gm) != gv) {
+            continue;
+          }
           double wr = Ff[3], wi = Ff[4];
           if (pt && (int)__double_as_longlong(Ff[5]) == pt->gate) {   // shifted circuit
             wr = pt->a0;

@@ -93,6 +93,10 @@ static_assert(sizeof(Op) == 64, "Op must stay 64 bytes");
 constexpr int DYADIC_BITS = 34;    // dyadic phases are multiples of 2 pi / 2^34
 constexpr int LPHASE_FAC = 6;      // doubles per OP_LPHASE factor: tile-local cm | cv << 32,
                                    // CTA cm, CTA cv, re, im, source gate
+// Marker in an OP_LPHASE factor's CTA cv: a parity factor, w on the
+// amplitudes with odd popcount(idx & mask) (mask = its tile-local cm, at most
+// one bit, and CTA cm), instead of the condition (idx & cm) == cv.
+constexpr uint64_t kLphaseParity = 1ull << 63;
 constexpr int DYADIC_HALF = 17;    // two-level table: 2^17 + 2^17 entries
 constexpr int MAX_TILE_BITS = 13;   // 2^13 amplitudes = 128 KiB of shared memory
 constexpr int PASS_HI_BITS = 9;    // pass_kernel maps up to 9 tile bits above the
@@ -237,6 +241,13 @@ struct ScheduleOptions {
   bool lphase_table = false; // mark one OP_LPHASE per pass for a per-CTA table,
                              // and OP_DPHASE ops for per-CTA partial-sum tables
                              // (schedules run by pass_kernel only)
+  bool sink_phases = false;  // move one-bit phases across passes to fewer merge
+                             // points (parity factors through CNOTs) and fold the
+                             // final scalar into a merged phase op of the last
+                             // pass (schedules run by pass_kernel only), for
+                             // states of at least sink_min_qubits qubits
+  int sink_min_qubits = 18;  // below it the search costs more host time than
+                             // the moved phases save on the device
 };
 
 // Per-state replacement of one gate's coefficients (shifted circuits of the
@@ -275,8 +286,10 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
 // complex multiply per affected amplitude).  With params = false, ops
 // of parametrised gates are left alone (per-circuit patches address them).
 void merge_dyadic(std::vector<LOp>& ops, int n, bool full_tables = false);
+// tile (nonzero): the pass's tile bits; parity phases (OP_PARITY) with at
+// most one tile bit then merge too, as parity factors.
 void merge_linear(std::vector<LOp>& ops, int n, bool params, std::vector<int>* src,
-                  int coef_budget);
+                  int coef_budget, uint64_t tile = 0);
 
 // Validate and lower a whole circuit at the given parameters.  The caller
 // owns *ops_out (delete[]).  (*zr, *zi) is the product of deferred factors.

@@ -306,6 +306,7 @@ lq_status lq_trotter_evolve(void* amps, int n, const lq_pauli_term* terms, int n
   ScheduleOptions opt;
   opt.lphase_table = true;   // run by pass_kernel
   opt.max_hi = PASS_HI_BITS;
+  opt.sink_phases = true;
   Schedule S;
   st = schedule_ops(n, ops.data(), ops.size(), zr, zi, opt, S);
   if (st) return st;

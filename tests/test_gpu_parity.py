@@ -80,6 +80,40 @@ def test_random_circuit(lq, n, seed, ng):
     np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
 
 
+@pytest.mark.parametrize("n,k,m,table,seed", [(18, 6, 2, 0, 1), (18, 8, 3, 1, 2), (19, 9, 4, 0, 3),
+                                              (18, 7, 5, 1, 4), (20, 10, 3, 0, 5)])
+def test_phase_sinking_across_many_passes(lq, tune_entry, n, k, m, table, seed):
+    # small forced tiles give many passes: one-bit phases (RZ, P, T) move
+    # forward across passes, through CNOT and CY targets and swaps as parity
+    # phases, and merge where at most one of their bits is a tile bit
+    rng = np.random.default_rng(900 + seed)
+    kinds = ["RY", "RZ", "RZ", "RZ", "P", "T", "CNOT", "CNOT", "CY", "SWAP", "CZ", "H", "RX", "CP"]
+    gates, P = W.random_circuit(n, 150, rng, kinds=kinds)
+    params = rng.uniform(-np.pi, np.pi, P)
+    psi = W.gaussian_state(n, 700 + seed)
+    want = oracle.apply_circuit(psi.copy(), n, gates, params)
+    tune_entry(n, gates, k, m, table)
+    t = dev(psi)
+    lq.apply_circuit(t, n, gates, params)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
+
+
+@pytest.mark.parametrize("n,depth,ent,k,m", [(18, 2, "ladder", 8, 3), (18, 3, "ring", 9, 2),
+                                             (22, 1, "ladder", 12, 3), (22, 2, "ring", 12, 3)])
+def test_hea_phases_merged_once_per_layer(lq, tune_entry, n, depth, ent, k, m):
+    # a layer's RZ factors reach its last pass as CTA-bit parities and
+    # one-bit tile phases, one merged op with the circuit's final scalar
+    rng = np.random.default_rng(n + depth)
+    gates, P = W.hea(n, depth, ent)
+    params = rng.uniform(-np.pi, np.pi, P)
+    psi = W.gaussian_state(n, 800 + n)
+    want = oracle.apply_circuit(psi.copy(), n, gates, params)
+    tune_entry(n, gates, k, m, 0)
+    t = dev(psi)
+    lq.apply_circuit(t, n, gates, params)
+    np.testing.assert_allclose(host(t), want, rtol=0, atol=ATOL)
+
+
 @pytest.mark.parametrize("name", sorted(oracle.GATE_CODES))
 def test_each_gate_kind_on_every_qubit_tuple(lq, name):
     n = 4

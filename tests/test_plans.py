@@ -33,11 +33,12 @@ def test_fft_qft_passes(n, passes):
     assert p["dram_bytes"] == (passes + 1) * 32 * 2.0 ** n
 
 
-@pytest.mark.parametrize("n,reads", [(24, 3), (30, 4)])
+@pytest.mark.parametrize("n,reads", [(20, 2), (24, 3), (30, 3)])
 def test_xyz_chain_expval_reads(n, reads):
     # 3(n-1) terms: one diagonal group (ZZ) and n-1 X-mask groups (XX+YY on a
-    # bond); a tile holds 12 bits, the 5 low ones fixed, so a pass covers the
-    # bonds inside 7 further bits
+    # bond); a tile holds 12 bits, the 2 low ones fixed, so the first pass
+    # covers the 11 bonds inside bits 0-11 and each later one the 9 bonds
+    # inside 10 further bits: 11 + 9 + 9 = 29 at n = 30
     terms = W.heisenberg(n)
     assert len(terms) == 3 * (n - 1)
     p = lq.expval_plan(n, terms)
@@ -72,3 +73,16 @@ def test_expval_plan_splits_passes_beyond_one_plan(n, masks, diag):
               for _ in range(diag)]
     p = lq.expval_plan(n, terms)
     assert p["npasses"] >= 2
+
+
+@pytest.mark.parametrize("k,m,passes", [(12, 3, 3), (10, 5, 5)])
+def test_hea_layer_one_merged_phase_op(tune_entry, k, m, passes):
+    # the layer's 30 RZ factors are applied once, in its last pass, as one
+    # merged phase op (12 flops per amplitude) that also takes the final
+    # scalar: 30 RY x 4 flops + 12 per amplitude, whatever the pass count
+    n = 30
+    gates, P = W.hea(n, 1, "ladder")
+    tune_entry(n, gates, k, m, 0)
+    p = lq.circuit_plan(n, gates, W.angles(P, 2030))
+    assert p["npasses"] == passes and p["tile_bits"] == k
+    assert p["dp_flops"] == (30 * 4 + 12) * 2.0 ** n
