@@ -50,7 +50,7 @@ FP64_NOMINAL_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # library.  tests/test_bench_cpu.py checks them against the library's plans.
 ORACLE_STEP_PASSES = {10: (1, 2, 2, 10), 11: (2, 2, 3, 11), 12: (2, 2, 3, 1), 13: (2, 3, 3, 2),
                       14: (2, 3, 3, 2), 15: (2, 3, 3, 2), 16: (3, 3, 4, 2), 17: (3, 3, 4, 2),
-                      18: (3, 3, 4, 2), 19: (3, 3, 4, 3), 20: (3, 3, 4, 3), 21: (4, 3, 5, 3),
+                      18: (3, 3, 4, 2), 19: (3, 3, 4, 2), 20: (3, 3, 4, 2), 21: (4, 3, 5, 2),
                       22: (4, 3, 5, 3), 23: (4, 4, 5, 3), 24: (4, 4, 5, 3)}
 
 
@@ -77,6 +77,8 @@ def parse():
                     help="seconds of CPU work the oracle sample spans at least")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="requests of the serving measurement (Poisson pass)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving measurement and print its JSON")
     return ap.parse_args()
 
 
@@ -274,9 +276,11 @@ class Step:
                                                launches=ap["npasses"])
         self.bytes = sum(r["bytes"] for r in self.rows.values())
 
-    def run(self, events=None, host_in=None):
+    def run(self, events=None, host_in=None, work=None):
         """One step; `events` (list of CUDA events, len 8) marks the rows.
-        host_in: pinned host tensor to copy in (e2e)."""
+        host_in: pinned host tensor to copy in (e2e); work: a device state
+        that already holds the step's input (e2e with the copy issued
+        earlier on a copy stream), used in place of the copy-in."""
         import ctypes
 
         import torch
@@ -290,19 +294,21 @@ class Step:
                 ev[i].record(s)
 
         mark(0)
-        if host_in is not None:
-            self.work.copy_(host_in, non_blocking=True)
-        else:
-            self.work.copy_(self.inp)
+        if work is None:
+            work = self.work
+            if host_in is not None:
+                work.copy_(host_in, non_blocking=True)
+            else:
+                work.copy_(self.inp)
         mark(1)
-        lq.apply_circuit(self.work, n, self.layer, self.theta)
+        lq.apply_circuit(work, n, self.layer, self.theta)
         mark(2)
-        lq.qft(self.work, n, method=lq.QFT_FFT)
+        lq.qft(work, n, method=lq.QFT_FFT)
         mark(3)
-        lq.qft(self.work, n, inverse=True, method=lq.QFT_GATES)
+        lq.qft(work, n, inverse=True, method=lq.QFT_GATES)
         mark(4)
         lq._check(lq.load().lq_expval_pauli_sum_async(
-            lq._ptr(self.work), n, self.packed_terms, len(self.terms),
+            lq._ptr(work), n, self.packed_terms, len(self.terms),
             ctypes.c_void_p(self.e_dev.data_ptr()), lq._ptr(self.exp_ws), self.exp_ws.numel(),
             ctypes.c_void_p(s.cuda_stream)))
         mark(5)
@@ -448,28 +454,65 @@ def bench_lq(a, rank, world, device):
 
 
 def e2e(step, a):
-    """Same step through the public API with host buffers: the input state
-    is copied from pinned host memory and the energy read back each step."""
+    """The same step through the public API with host buffers: every step's
+    input state is copied from pinned host memory and its energy read back
+    (a synchronous device-to-host copy) inside the timed region.  The copies
+    run one step ahead on a copy stream into a second device state, so step
+    k+1's 16 GiB copy overlaps step k's kernels (the first step's copy is not
+    overlapped); a device state is refilled only after the step that used it
+    has finished.  `serial_ms_per_step` is the same loop with each copy
+    issued on the compute stream right before its step."""
     import torch
 
     host = torch.empty(step.inp.shape, dtype=step.inp.dtype, pin_memory=True)
     host.copy_(step.inp)
     out_host = torch.empty(1, dtype=torch.float64, pin_memory=True)
-    for _ in range(max(3, a.warmup)):   # the first copies from a fresh pinned buffer can be slower
-        step.run(host_in=host)
-        out_host.copy_(step.e_dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    k = max(2, a.steps // 2)
-    for _ in range(k):
-        step.run(host_in=host)
-        out_host.copy_(step.e_dev)   # synchronous device->host read of <H>
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / k
-    del host
+    bufs = [step.work, torch.empty_like(step.work)]
+    cs = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+
+    def pipelined(k):
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        free = [None, None]
+        with torch.cuda.stream(cs):
+            bufs[0].copy_(host, non_blocking=True)
+            copied[0].record(cs)
+        for i in range(k):
+            if i + 1 < k:   # the next step's input, into the other state
+                j = (i + 1) % 2
+                with torch.cuda.stream(cs):
+                    if free[j] is not None:
+                        cs.wait_event(free[j])
+                    bufs[j].copy_(host, non_blocking=True)
+                    copied[j].record(cs)
+            main.wait_event(copied[i % 2])
+            step.run(work=bufs[i % 2])
+            free[i % 2] = torch.cuda.Event()
+            free[i % 2].record(main)
+            out_host.copy_(step.e_dev)   # synchronous device->host read of <H>
+
+    def serial(k):
+        for _ in range(k):
+            step.run(host_in=host)
+            out_host.copy_(step.e_dev)
+
+    k = max(3, a.steps)
+    res = {}
+    for name, loop in (("pipelined", pipelined), ("serial", serial)):
+        loop(max(3, a.warmup))   # the first copies from a fresh pinned buffer can be slower
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loop(k)
+        torch.cuda.synchronize()
+        res[name] = (time.perf_counter() - t0) / k
+    del host, bufs
+    dt = res["pipelined"]
     return {"value": round(step.bytes / dt / 1e9, 2), "unit": UNIT,
             "h2d_bytes_per_step": int(step.inp.numel() * 16), "d2h_bytes_per_step": 8 + 8 * 81,
-            "ms_per_step": round(dt * 1e3, 3)}
+            "ms_per_step": round(dt * 1e3, 3), "steps": k,
+            "serial_ms_per_step": round(res["serial"] * 1e3, 3),
+            "how": "host-timed over %d steps; input copies one step ahead on a copy stream "
+                   "(double-buffered device state), energy read back every step" % k}
 
 
 # ------------------------------------------------------- side measurements
@@ -517,9 +560,10 @@ def vqe_extras(device):
             pass
         r["circuits_per_grad"] = 2 * len(th) + 1
         res[name] = r
-    # adjoint workload: n=24, depth-10 ladder, 480 angles (seed 5), open chain.
-    # A parameter-shift gradient here is 961 full circuits; its rate is given
-    # from the measured time of one circuit (|0..0> -> <H>), labelled as such.
+    # adjoint workload: n=24, depth-10 ladder, 480 angles (seed 5), open chain:
+    # the adjoint gradient, the batched parameter-shift gradient (all 961
+    # circuits in one persistent launch, one timed run), their agreement, and
+    # one plain circuit (|0..0> -> <H>) for the plain method's rate
     n = 24
     gates, P = W.hea(n, 10, "ladder")
     th = W.angles(P, 5)
@@ -529,10 +573,27 @@ def vqe_extras(device):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(3):
-        lq.adjoint_grad(n, gates, th, terms, device=device)
+        ea, ga = lq.adjoint_grad(n, gates, th, terms, device=device)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / 3
     r["adjoint"] = {"grads_per_s": round(1.0 / dt, 3), "ms": round(dt * 1e3, 3)}
+    ws = torch.empty(lq.load().lq_param_shift_workspace_size(n, P, len(terms), lq.PSR_BATCHED),
+                     dtype=torch.uint8, device=device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eb, gb = lq.param_shift_grad(n, gates, th, terms, method=lq.PSR_BATCHED, workspace=ws)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    r["batched"] = {"grads_per_s": round(1.0 / dt, 4), "ms": round(dt * 1e3, 1),
+                    "workspace_gb": round(ws.numel() / 1e9, 1),
+                    "note": "one run (the graph capture, a few ms, included)"}
+    tol = 1e-10 * max(1.0, float(abs(gb).max()))
+    r["adjoint_vs_batched"] = {"max_abs_dgrad": float(abs(ga - gb).max()),
+                               "abs_denergy": abs(ea - eb), "tolerance": tol,
+                               "agree": bool(abs(ga - gb).max() <= tol
+                                             and abs(ea - eb) <= 1e-10 * max(1.0, abs(eb)))}
+    del ws
+    torch.cuda.empty_cache()
     psi = lq.new_state(n)
     ws = torch.empty(lq.load().lq_expval_workspace_size(n, len(terms)), dtype=torch.uint8,
                      device=device)
@@ -549,7 +610,7 @@ def vqe_extras(device):
         circuit()
     dt1 = (time.perf_counter() - t0) / 3
     r["one_circuit_ms"] = round(dt1 * 1e3, 3)
-    r["psr_grads_per_s_from_one_circuit"] = round(1.0 / (dt1 * (2 * P + 1)), 4)
+    r["plain_grads_per_s_from_one_circuit"] = round(1.0 / (dt1 * (2 * P + 1)), 4)
     r["circuits_per_grad"] = 2 * P + 1
     res["adjoint_n24_d10_480p"] = r
     del psi, ws
@@ -810,6 +871,13 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     device = "cuda:%d" % local
+    if a.serve_only:
+        if rank == 0:
+            import paper_2512_23183_gb300 as lq
+
+            lq.load()
+            print(json.dumps({"serve": serve_extras(device, count=a.serve_requests)}), flush=True)
+        return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device(device))
     out, step = bench_lq(a, rank, world, device)

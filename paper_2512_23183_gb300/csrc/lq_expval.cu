@@ -57,7 +57,7 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
   wide.clear();
   if (kt > XP_TILE_BITS) kt = XP_TILE_BITS;
   const int k = n < kt ? n : kt;
-  const int m0 = n < 5 ? n : 5;
+  const int m0 = n < XP_LOW_BITS ? n : XP_LOW_BITS;
   const uint64_t low = (1ull << m0) - 1ull;
 
   // groups by X mask; groups with x != 0 that cannot use class mode are split
@@ -370,7 +370,9 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
   // dynamic shared memory: the tile, then the coefficient table, then the
   // diagonal chunk tables
   extern __shared__ double2 xsm[];
-  __shared__ uint32_t hioff[1 << (XP_TILE_BITS - 5)];   // k - m <= XP_TILE_BITS - 5
+  // global offsets (>> m) of the tile bits above the low run: off(j) =
+  // hlo[j & 31] | hhi[j >> 5] (k - m <= XP_TILE_BITS - XP_LOW_BITS = 10 bits)
+  __shared__ uint32_t hlo[32], hhi[1 << (XP_TILE_BITS - XP_LOW_BITS - 5)];
   __shared__ double red[BLOCK / 32];
   const uint32_t tid = threadIdx.x;
   const double2* __restrict__ st = states + blockIdx.y * stride;
@@ -400,15 +402,20 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
     const int k = Q.k, m = Q.m, kh = k - m;
     const uint32_t T = 1u << k, lowmask = (1u << m) - 1u;
     __syncthreads();
-    for (uint32_t j = tid; j < (1u << kh); j += BLOCK)
-      hioff[j] = (uint32_t)(deposit(j, Q.tbits + m, kh) >> m);
+    if (tid < 32) {
+      const int kl = kh < 5 ? kh : 5;
+      hlo[tid] = tid < (1u << kl) ? (uint32_t)(deposit(tid, Q.tbits + m, kl) >> m) : 0u;
+      if (tid < (1u << (XP_TILE_BITS - XP_LOW_BITS - 5)))
+        hhi[tid] = kh > 5 ? (uint32_t)(deposit((uint64_t)tid << 5, Q.tbits + m, kh) >> m) : 0u;
+    }
     __syncthreads();
+    auto hioff = [&](uint32_t j) { return hlo[j & 31u] | hhi[j >> 5]; };
     const uint64_t ntiles = 1ull << (n - k);
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const uint64_t base = deposit(t, Q.obits, Q.nobits);
       const double2* __restrict__ sm = xsm;
       for (uint32_t s = tid; s < T; s += BLOCK)
-        xsm[s] = st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)];
+        xsm[s] = st[base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask)];
       __syncthreads();
       for (int g = Q.g0; g < Q.g1; g++) {
         const XGroup& G = X.groups[g];
@@ -421,7 +428,7 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
             acc += xp_class_group<BLOCK, 2>(sm, T, G, coef);
         } else if (G.mode == XG_DIAG) {
           for (uint32_t s = tid; s < T; s += BLOCK) {
-            const uint64_t gi = base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask);
+            const uint64_t gi = base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask);
             const double2 v = sm[s];
             const double pr = fma(v.x, v.x, v.y * v.y);
             double d = 0.0;

@@ -45,6 +45,7 @@ static_assert(sizeof(ExpParams) < 32000, "ExpParams exceeds the kernel parameter
 // Tiled <H> (lq_expval.cu): terms grouped by X mask, groups packed into tile
 // passes whose tile bits cover their X masks.
 constexpr int XP_TILE_BITS = 12;   // largest tile (the plan picks 11 or 12)
+constexpr int XP_LOW_BITS = 2;     // contiguous low bits in every tile (64-byte runs)
 constexpr int kTiledExpvalMinN = 12;   // smaller states use the untiled kernel
 constexpr int XP_MAX_PASS = 48;
 constexpr int XP_MAX_GROUPS = 192;
