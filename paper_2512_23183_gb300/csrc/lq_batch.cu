@@ -441,15 +441,35 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B,
   return LQ_OK;
 }
 
+// Device memory the per-CTA scratch states of one launch may take: 40% of
+// the device's memory (115 GB on a GB300), at least 4 GiB.
+static std::size_t scratch_budget() {
+  static std::size_t cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    (void)cudaGetLastError();
+    return (std::size_t)48 << 30;
+  }
+  if (!cached[dev]) {
+    cudaDeviceProp pr;
+    std::size_t total = 0;
+    if (cudaGetDeviceProperties(&pr, dev) == cudaSuccess) total = pr.totalGlobalMem;
+    (void)cudaGetLastError();
+    std::size_t b = total / 10 * 4;
+    cached[dev] = b < ((std::size_t)4 << 30) ? ((std::size_t)4 << 30) : b;
+  }
+  return cached[dev];
+}
+
 static int batch_grid(const BatchPlan& B) {
   std::size_t smem = sizeof(double2) << B.kmax;
   int per_sm = smem <= 16384 ? 6 : smem <= 32768 ? 4 : smem <= 65536 ? 3 : 1;
   int g = sm_count() * per_sm;
   if ((int)B.items.size() < g) g = (int)B.items.size();
   if (B.nmax_scratch > 0) {
-    // keep the scratch states within 48 GiB
+    // keep the scratch states within the device's scratch budget
     std::size_t sb = sizeof(double2) << B.nmax_scratch;
-    std::size_t cap = ((std::size_t)48 << 30) / sb;
+    std::size_t cap = scratch_budget() / sb;
     if (cap < 1) cap = 1;
     if ((std::size_t)g > cap) g = (int)cap;
   }

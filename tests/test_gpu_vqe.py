@@ -36,8 +36,10 @@ def test_vqe_adam_follows_reference(method):
     th, es = lq.vqe_adam(n, gates, th0, terms, max_iters=40, tol=0.0, method=method)
     th_w, es_w = reference_adam(n, gates, th0, terms, 40)
     assert es.size == 40
-    np.testing.assert_allclose(es, es_w, rtol=0, atol=1e-9)
-    np.testing.assert_allclose(th, th_w, rtol=0, atol=1e-9)
+    # energies within the 1e-10 relative energy tolerance; the parameters
+    # Adam derives from the gradients within the same bound
+    np.testing.assert_allclose(es, es_w, rtol=0, atol=1e-10 * max(1.0, np.abs(es_w).max()))
+    np.testing.assert_allclose(th, th_w, rtol=0, atol=1e-10)
 
 
 def test_vqe_adam_converges_above_ground_energy():
