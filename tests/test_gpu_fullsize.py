@@ -205,3 +205,25 @@ def test_uneven_batch_config_sample(lq):
     p[3] -= np.pi
     em = oracle.energy(n, g, p, t)
     assert abs(probs[j].grad[3] - 0.5 * (ep - em)) <= RTOL * max(1.0, abs(probs[j].grad[3]))
+
+
+def test_adjoint_vs_batched_psr_n24_config(lq):
+    # the adjoint workload as configured (n = 24, depth-10 ladder, 480 angles
+    # seed 5, open chain): the adjoint gradient against the batched
+    # parameter-shift gradient (all 961 circuits in one persistent launch) on
+    # every entry, and the batched energy against the oracle
+    import torch
+
+    n = 24
+    gates, P = W.hea(n, 10, "ladder")
+    th = W.angles(P, 5)
+    terms = W.heisenberg(n)
+    ea, ga = lq.adjoint_grad(n, gates, th, terms)
+    ws = torch.empty(lq.load().lq_param_shift_workspace_size(n, P, len(terms), lq.PSR_BATCHED),
+                     dtype=torch.uint8, device="cuda")
+    eb, gb = lq.param_shift_grad(n, gates, th, terms, method=lq.PSR_BATCHED, workspace=ws)
+    del ws
+    torch.cuda.empty_cache()
+    assert _close(ea, eb)
+    np.testing.assert_allclose(ga, gb, rtol=0, atol=RTOL * max(1.0, np.abs(gb).max()))
+    assert _close(eb, oracle.energy(n, gates, th, terms))
