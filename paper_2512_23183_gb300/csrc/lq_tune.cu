@@ -159,9 +159,12 @@ lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng
   // 4 at k = 11, m = 4 instead of 5 at m = 5)
   for (int k = kmax < 9 ? kmax : 9; k <= kmax; k++)
     for (int m = k >= 11 ? 3 : 5; m <= 6; m++)
-      // the per-CTA phase table exists for tiles of up to 2^LTAB_MAX_BITS
-      // amplitudes; above that both settings give the same schedule
-      for (int table = k <= LTAB_MAX_BITS ? 1 : 0; table >= 0; table--) {
+      // the option switches the per-CTA tables: a one-bit phase op's table
+      // (tiles of up to 2^LTAB_MAX_BITS amplitudes) and the merged dyadic
+      // phases' partial-sum and full tables (any tile; the gate-form QFT's
+      // butterflies need them).  Above 2^LTAB_MAX_BITS the option only
+      // changes the dyadic tables, which are never slower: only "on" is timed
+      for (int table = 1; table >= (k <= LTAB_MAX_BITS ? 0 : 1); table--) {
         const int mm = m < k ? m : k;
         bool dup = false;
         for (const Cand& c : cands) dup |= c.k == k && c.m == mm && c.table == table;
@@ -176,6 +179,7 @@ lq_status lq_autotune_circuit(void* scratch, int n, const lq_gate* gates, int ng
     opt.m = c.m;
     opt.max_hi = PASS_HI_BITS;
     opt.lphase_table = c.table != 0;
+    opt.sink_phases = true;   // as lq_apply_circuit schedules
     Schedule S;
     st = schedule_ops(n, ops, nops, zr, zi, opt, S);
     if (st) {

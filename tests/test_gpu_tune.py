@@ -159,3 +159,21 @@ def test_autotune_qft_gate_form(lq):
     np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
     assert lq.qft_plan(n, lq.QFT_GATES)["npasses"] >= 2
     del torch
+
+
+def test_autotune_inverse_gate_qft_keeps_dyadic_tables(lq):
+    # the table option also switches the merged dyadic phases' tables (the
+    # gate-form QFT's butterflies); the tuner must time 2^11 and 2^12 tiles
+    # with them: at n = 26 the best schedule keeps them, beats the default,
+    # and the transform still equals the oracle's inverse DFT
+    n = 26
+    r = lq.autotune_qft(n, inverse=True)
+    lq_plan = lq.qft_plan(n, lq.QFT_GATES, inverse=True)
+    assert r["phase_table"] == 1 and r["ms"] <= r["ms_default"]
+    assert lq_plan["tile_bits"] == r["tile_bits"]
+    psi = W.gaussian_state(n, 1000 + n)
+    t = _dev(psi)
+    lq.qft(t, n, inverse=True, method=lq.QFT_GATES)
+    want = oracle.qft_fft(psi.copy(), n, inverse=True)
+    np.testing.assert_allclose(t.cpu().numpy(), want, rtol=0, atol=ATOL)
+    lq.tune_cache_clear()
