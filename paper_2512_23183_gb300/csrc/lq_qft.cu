@@ -18,6 +18,18 @@
 // (four-step FFT).  Local twiddles come from a constant table in tangent form
 // (c, t = s/c) or cotangent form (s, u = c/s), so each butterfly costs
 // 6 FP64 FMAs: b' = b + i t b (2), a +- c b' (4).
+//
+// Radix 4.  Stages r and r + 1 of a pass act on local bits p and p - 1; on a
+// quad x_ab (a = bit p, b = bit p - 1, v = the in-tile bits above p,
+// theta = pi bitrev_r(v) / 2^{r+1}) stage r's twiddle is W1 = e^{2 i theta}
+// and stage r + 1's is W2 = e^{i theta} where a = 0 and i W2 where a = 1, so
+//   z_00, z_01 = (x00 + W1 x10) +- (W2 x01 + W3 x11),
+//   z_10, z_11 = (x00 - W1 x10) +- i (W2 x01 - W3 x11),   W3 = W1 W2,
+// the classic radix-4 step.  With each W = c (1 + i sigma) applied to x or
+// to i x (2 FMAs) and c1, c2, rho = c3 / c2 folded into the sums, a quad
+// costs 22 FMAs instead of the 24 of two radix-2 stages, and one
+// shared-memory round trip instead of two.  A pass's first two stages have
+// unit twiddles (16 adds per quad); an odd last stage runs radix 2.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -54,13 +66,58 @@ __global__ void fft_table_kernel() {
   g_tw[idx] = cot ? make_double2(s, c / s) : make_double2(c, -s / c);
 }
 
-static cudaError_t fill_fft_table(cudaStream_t ps) {
-  fft_table_kernel<<<(FFT_TABLE + 255) / 256, 256, 0, ps>>>();
-  return cudaGetLastError();
-}
+
 
 // The twiddle table is filled once per device and complete before this
 // returns (fill_table_once), whichever thread or stream asks first.
+// g_tw4[3 ((1 << r) - 2 + v) + {0, 1, 2}]: the radix-4 twiddles of stages
+// (r, r + 1), r = 1 .. FFT_MAX_D - 2, for the in-tile bits v above stage r's
+// bit: (c1, sigma1) of W1, (c2, sigma2) of W2, (rho = c3 / c2, sigma3) of W3,
+// W3's sign (e^{3 i theta} = -e^{i (3 theta - pi)} when 3 theta >= pi) in c3.
+// With N = 2^{r+1} and u = bitrev_r(v) the angles are pi a / N for a = 2u, u
+// and 3u mod N; a twiddle is in cotangent form (scale sin, sigma = -cot) when
+// a lies in [N/4, 3N/4), else in tangent form (scale cos, sigma = tan), so
+// |sigma| <= 1 and |scale| >= 1/sqrt2 (|rho| in [1/sqrt2, sqrt2]).
+constexpr int FFT4_ENTRIES = (2 << (FFT_MAX_D - 2)) - 2;   // sum_{r=1}^{10} 2^r
+__device__ double2 g_tw4[3 * FFT4_ENTRIES];
+
+__host__ __device__ __forceinline__ bool fft4_cot(uint32_t a, uint32_t N) {
+  return ((a + 3u * (N >> 2)) & (N - 1u)) < (N >> 1);
+}
+
+__global__ void fft4_table_kernel() {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= FFT4_ENTRIES) return;
+  const int r = 31 - __clz(idx + 2);
+  const uint32_t v = (uint32_t)(idx + 2 - (1 << r));
+  const uint32_t u = __brev(v) >> (32 - r), N = 2u << r;
+  auto form = [&](uint32_t a, double* scale, double* sig) {
+    double sn, cs;
+    sincospi((double)a / (double)N, &sn, &cs);
+    if (fft4_cot(a, N)) {
+      *scale = sn;
+      *sig = -cs / sn;
+    } else {
+      *scale = cs;
+      *sig = sn / cs;
+    }
+  };
+  double c1, s1, c2, s2, c3, s3;
+  form(2u * u, &c1, &s1);
+  form(u, &c2, &s2);
+  form((3u * u) & (N - 1u), &c3, &s3);
+  if (3u * u >= N) c3 = -c3;
+  g_tw4[3 * idx] = make_double2(c1, s1);
+  g_tw4[3 * idx + 1] = make_double2(c2, s2);
+  g_tw4[3 * idx + 2] = make_double2(c3 / c2, s3);
+}
+
+static cudaError_t fill_fft_table(cudaStream_t ps) {
+  fft_table_kernel<<<(FFT_TABLE + 255) / 256, 256, 0, ps>>>();
+  fft4_table_kernel<<<(FFT4_ENTRIES + 255) / 256, 256, 0, ps>>>();
+  return cudaGetLastError();
+}
+
 cudaError_t fft_tables_init(cudaStream_t s) {
   (void)cudaGetLastError();  // report only this launcher's own errors
   static TableOnce once;
@@ -87,6 +144,67 @@ __device__ __forceinline__ void fft_bfly(double2& a, double2& b, double2 w, uint
   const double tr = fma(sg, q, p), ti = fma(-sg, p, q);
   b = make_double2(fma(-w.x, tr, a.x), fma(-w.x, ti, a.y));
   a = make_double2(fma(w.x, tr, a.x), fma(w.x, ti, a.y));
+}
+
+// x' with W x = scale x': W = scale (1 + i sigma) applied to x (tangent
+// form) or to i x (cotangent form); the inverse transform takes conj(W)
+// (sign masks fpos, fneg as in fft_bfly).  2 FMAs.
+__device__ __forceinline__ double2 fft4_rot(double2 x, double sig, bool cot, uint32_t fpos,
+                                            uint32_t fneg) {
+  const double p = cot ? xsign(x.y, fneg) : x.x;
+  const double q = cot ? xsign(x.x, fpos) : x.y;
+  const double sg = xsign(sig, fpos);
+  return make_double2(fma(-sg, q, p), fma(sg, p, q));
+}
+
+// A pass's first two stages (local bits lp and lp - 1; unit twiddles, and
+// i on the second stage where bit lp is set): 16 adds per quad.
+template <int BLOCK>
+__device__ __forceinline__ void fft4_first(double2* __restrict__ sm, uint32_t T, int lp,
+                                           uint32_t fpos, uint32_t fneg) {
+  const uint32_t L = 1u << lp, H = L >> 1;
+  for (uint32_t j = threadIdx.x; j < (T >> 2); j += BLOCK) {
+    const uint32_t s = insert0(insert0(j, lp - 1), lp);
+    const double2 x00 = sm[s], x01 = sm[s | H], x10 = sm[s | L], x11 = sm[s | L | H];
+    const double2 A = make_double2(x00.x + x10.x, x00.y + x10.y);
+    const double2 B = make_double2(x00.x - x10.x, x00.y - x10.y);
+    const double2 F1 = make_double2(x01.x + x11.x, x01.y + x11.y);
+    const double2 F2 = make_double2(x01.x - x11.x, x01.y - x11.y);
+    const double ix = xsign(F2.y, fneg), iy = xsign(F2.x, fpos);   // (+-i) F2
+    sm[s] = make_double2(A.x + F1.x, A.y + F1.y);
+    sm[s | H] = make_double2(A.x - F1.x, A.y - F1.y);
+    sm[s | L] = make_double2(B.x + ix, B.y + iy);
+    sm[s | L | H] = make_double2(B.x - ix, B.y - iy);
+  }
+}
+
+// Stages r and r + 1 (r >= 1) on local bits lp and lp - 1 as radix-4 steps
+// with the g_tw4 twiddles of level r: 22 FMAs per quad.
+template <int BLOCK>
+__device__ __forceinline__ void fft4_step(double2* __restrict__ sm, uint32_t T, int lp, int r,
+                                          uint32_t fpos, uint32_t fneg) {
+  const uint32_t L = 1u << lp, H = L >> 1, N = 2u << r;
+  const double2* __restrict__ t4 = g_tw4 + 3 * ((1 << r) - 2);
+  for (uint32_t j = threadIdx.x; j < (T >> 2); j += BLOCK) {
+    const uint32_t s = insert0(insert0(j, lp - 1), lp);
+    const double2 x00 = sm[s], x01 = sm[s | H], x10 = sm[s | L], x11 = sm[s | L | H];
+    const uint32_t v = s >> (lp + 1);
+    const uint32_t u = __brev(v) >> (32 - r);
+    const double2 e1 = t4[3 * v], e2 = t4[3 * v + 1], e3 = t4[3 * v + 2];
+    const double2 a = fft4_rot(x10, e1.y, fft4_cot(2u * u, N), fpos, fneg);
+    const double2 b = fft4_rot(x01, e2.y, fft4_cot(u, N), fpos, fneg);
+    const double2 c = fft4_rot(x11, e3.y, fft4_cot(3u * u, N), fpos, fneg);
+    const double c1 = e1.x, c2 = e2.x, rho = e3.x;
+    const double2 A = make_double2(fma(c1, a.x, x00.x), fma(c1, a.y, x00.y));
+    const double2 B = make_double2(fma(-c1, a.x, x00.x), fma(-c1, a.y, x00.y));
+    const double2 F1 = make_double2(fma(rho, c.x, b.x), fma(rho, c.y, b.y));
+    const double2 F2 = make_double2(fma(-rho, c.x, b.x), fma(-rho, c.y, b.y));
+    const double cn = xsign(c2, fneg);   // B +- (+-i) c2 F2
+    sm[s] = make_double2(fma(c2, F1.x, A.x), fma(c2, F1.y, A.y));
+    sm[s | H] = make_double2(fma(-c2, F1.x, A.x), fma(-c2, F1.y, A.y));
+    sm[s | L] = make_double2(fma(cn, F2.y, B.x), fma(-cn, F2.x, B.y));
+    sm[s | L | H] = make_double2(fma(-cn, F2.y, B.x), fma(cn, F2.x, B.y));
+  }
 }
 
 // One pass of the FFT form over the d qubits [q0, q1) (tile: those bits plus
@@ -144,8 +262,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F
       sm[s] = v;
     }
     __syncthreads();
-    // stage r: qubit q0 + r acts on local bit lp = ms + d - 1 - r
-    {
+    // stage r: qubit q0 + r acts on local bit lp = ms + d - 1 - r; stages
+    // in pairs as radix-4 steps, an odd last one radix 2
+    int r = 0;
+    if (d >= 2) {
+      fft4_first<BLOCK>(sm, T, ms + d - 1, fpos, fneg);
+      __syncthreads();
+      r = 2;
+    } else {
       const int lp = ms + d - 1;
       const uint32_t L = 1u << lp;
       for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
@@ -155,8 +279,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F
         sm[s0 | L] = make_double2(a.x - b.x, a.y - b.y);
       }
       __syncthreads();
+      r = 1;
     }
-    for (int r = 1; r < d; r++) {
+    for (; r + 1 < d; r += 2) {
+      fft4_step<BLOCK>(sm, T, ms + d - 1 - r, r, fpos, fneg);
+      __syncthreads();
+    }
+    if (r < d) {
       const int lp = ms + d - 1 - r;
       const uint32_t L = 1u << lp;
       const double2* tw = g_tw + ((1 << r) - 1);
@@ -406,8 +535,10 @@ extern "C" lq_status lq_qft_plan_dir(int n, int method, int inverse, lq_plan_inf
     int d = b[p + 1] - b[p];
     int ms = (n - b[p + 1]) < 3 ? (n - b[p + 1]) : 3;
     kmax = kmax > d + ms ? kmax : d + ms;
-    // butterflies: first stage 2 adds per amplitude, others 6 FMA per pair
-    fl += N * (2.0 + 6.0 * (d - 1));
+    // butterflies: the first two stages 16 adds per quad, later pairs of
+    // stages 22 FMA per quad (radix 4), an odd last stage 6 FMA per pair; a
+    // one-stage pass 2 adds per amplitude
+    fl += d == 1 ? 2.0 * N : N * (4.0 + 11.0 * ((d - 2) / 2) + 6.0 * ((d - 2) % 2));
     // diagonal of the pass (all but the first; the last also carries the scale)
     if (p > 0 || b.size() == 2) fl += 6.0 * N;
   }

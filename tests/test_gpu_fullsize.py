@@ -9,9 +9,10 @@ properties that hold at any size.
   - VQE n = 10 depth 4, 80 angles seed 1: energy and full gradient;
   - batched PSR n = 16 depth 8 ring, 256 angles seed 3: energy by the oracle,
     sampled gradient entries by oracle energies at +-pi/2;
-  - adjoint n = 24 depth 10, 480 angles seed 5: energy by the oracle, sampled
-    entries against GPU parameter shift (1e-10) and central differences
-    (h = 1e-4, 1e-6);
+  - adjoint n = 24 depth 10, 480 angles seed 5: energy and the first and
+    last gradient entries by the oracle, sampled entries against GPU
+    parameter shift (1e-10) and central differences (h = 1e-4, 1e-6), every
+    entry against the batched parameter-shift launch;
   - uneven batch: a sample of the 64 seeded instances against the oracle.
 """
 import numpy as np
@@ -180,8 +181,16 @@ def test_adjoint_n24_config_sampled(lq):
         p[i] -= 2e-4
         fm = energy(p)
         assert abs(g[i] - (fp - fm) / 2e-4) < 1e-6, i
-    # the energy itself by the oracle (one evaluation at 2^24 amplitudes)
+    # the energy itself by the oracle (one evaluation at 2^24 amplitudes), and
+    # the first and last gradient entries by the oracle's energies at +-pi/2
     assert _close(e, oracle.energy(n, gates, th, terms))
+    for i in (0, P - 1):
+        p = th.copy()
+        p[i] += np.pi / 2
+        ep = oracle.energy(n, gates, p, terms)
+        p[i] -= np.pi
+        em = oracle.energy(n, gates, p, terms)
+        assert abs(g[i] - 0.5 * (ep - em)) <= RTOL * max(1.0, abs(g[i])), i
 
 
 def test_uneven_batch_config_sample(lq):
