@@ -921,22 +921,26 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
       // full tables with the per-tile phases deferred to the store or the load;
       // a full-mode op's partial sums are built in the (still unused) tile
       // buffer, so only its CTA-decided factor triples stay resident
-      int entries = 0, nd = 0;
+      int entries = 0, nd = 0, nfull = 0;
       uint32_t ubits = 0;
       const int scratch_slots = (2 << k) / 256;   // 256-word tables the tile buffer holds
       for (int o = 0; o < cnt && (P.h.flags & PF_DTAB); o++) {
         Op& d = P.ops[o];
-        if (d.type != OP_DPHASE || !(d.mode & DP_TABLE) || nd == 8 || nd >= scratch_slots)
-          continue;
+        if (d.type != OP_DPHASE || !(d.mode & DP_TABLE) || nfull >= scratch_slots) continue;
         const int c = __builtin_popcount(d.cm_loc);
         if (c < 1) continue;
+        // no CTA-decided factor and no CTA-bit condition: the phase is the
+        // same for every tile, there is no per-tile part to defer, and the op
+        // needs no deferred slot
+        const bool local = d.b1 == 0 && d.cm_glob == 0;
+        if (!local && nd == 8) continue;
         const int sz = 1 << (k - c);
         // the per-tile part commutes to the store if no later op of the pass
         // mixes a condition bit, else to the load if no earlier op does
         bool later = false, earlier = false;
         for (int o2 = o + 1; o2 < cnt; o2++) later |= (op_mixing_bits(P.ops[o2]) & d.cm_loc) != 0;
         for (int o2 = 0; o2 < o; o2++) earlier |= (op_mixing_bits(P.ops[o2]) & d.cm_loc) != 0;
-        if (later && earlier) continue;
+        if (later && earlier && !local) continue;
         // butterfly with the H on its condition bit right after it (DP_BFLY):
         // the table is followed by one form byte per entry; its per-CTA build
         // (a division per entry) pays off from 2^12 tiles on (measured:
@@ -963,10 +967,13 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
           if (bfly) bsz = 1 << width;
         }
         const int need = bfly ? bsz + (bsz + 15) / 16 : sz;
-        if (entries + need > DFULL_MAX_ENTRIES || __builtin_popcount(ubits | d.cm_loc) > 6)
+        if (entries + need > DFULL_MAX_ENTRIES ||
+            (!local && __builtin_popcount(ubits | d.cm_loc) > 6))
           continue;
         d.mode |= DP_FULL;
-        if (later) {
+        if (local) {
+          d.mode |= DP_NODEFER;
+        } else if (later) {
           d.mode |= DP_PRE;
           P.h.dpre |= (uint8_t)(1u << nd);
         }
@@ -977,12 +984,19 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
           d.b = width;
         }
         d.z_glob = (uint64_t)entries;
-        d.b0 = (uint8_t)nd;
+        d.b0 = (uint8_t)nd;   // deferred slot (local ops: renumbered below)
         entries += need;
-        ubits |= d.cm_loc;
-        nd++;
+        if (!local) {
+          ubits |= d.cm_loc;
+          nd++;
+        }
+        nfull++;
       }
-      if (nd) {
+      // b0 is also the op's scratch slot for building its table in the tile
+      // buffer: the deferred ops keep their slots 0..nd-1, local ones follow
+      for (int o = 0, sl = nd; o < cnt; o++)
+        if (P.ops[o].type == OP_DPHASE && (P.ops[o].mode & DP_NODEFER)) P.ops[o].b0 = (uint8_t)sl++;
+      if (entries) {
         // re-lay the resident area: full-mode ops keep their triples only
         uint32_t w2 = 0;
         for (int o = 0; o < cnt; o++) {
@@ -1005,7 +1019,7 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
         };
         for (int o = 0; o < cnt; o++) {
           const Op& d = P.ops[o];
-          if (d.type != OP_DPHASE || !(d.mode & DP_FULL)) continue;
+          if (d.type != OP_DPHASE || !(d.mode & DP_FULL) || (d.mode & DP_NODEFER)) continue;
           P.h.dmask[d.b0] = squeeze(d.cm_loc);
           P.h.dval[d.b0] = squeeze(d.cv_loc);
         }

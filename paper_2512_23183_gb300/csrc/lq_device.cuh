@@ -691,7 +691,7 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
         if ((op.mode & DP_FULL) && tabs->dfull) {
           // tile-invariant part from the full table; e0 deferred to the store
           // (summed here) or to the load (summed when the tile started)
-          if (!(op.mode & DP_PRE)) {
+          if (!(op.mode & (DP_PRE | DP_NODEFER))) {
             const unsigned long long e0 = dphase_tile_sum(tb, (int)op.b1, base);   // triples
             if (tid == 0) tabs->dfe[op.b0] = e0;
           }

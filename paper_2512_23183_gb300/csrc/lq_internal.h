@@ -175,6 +175,10 @@ constexpr uint8_t DP_PRE = 0x20;
 // factors' tile bits only, which form one run of tile-local positions
 // [a, a + b) (Op::a, Op::b): the table has 2^b entries, index (s >> a) mod 2^b.
 constexpr uint8_t DP_BFLY = 0x10;
+// A full-mode OP_DPHASE with no CTA-decided factor and no CTA-bit condition:
+// its phase is the same for every tile, so it has no per-tile part and takes
+// no deferred slot (Op::b0 is then only its scratch slot for the table build).
+constexpr uint8_t DP_NODEFER = 0x08;
 constexpr int DFULL_MAX_ENTRIES = 3072;     // per pass (48 KiB of shared memory)
 
 // OP_LPHASE in table mode (Op::mode bit): every factor's condition bit is a
