@@ -761,13 +761,31 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
     int coefs = 0, grads = 0;
     std::vector<int> skipped;
     uint64_t blocked_mix = 0, blocked_all = 0;
-    for (int idx : pending) {
+    // a merged dyadic phase on one condition bit c that can no longer join
+    // this pass's tile, whose next op on c is the H on c: in the pass that
+    // holds c the two run
+    // as one butterfly (or at least as a full-table phase op), here it would
+    // run on every amplitude of half the tiles; it waits for that pass
+    auto waits_for_h = [&](std::size_t pi) {
+      const LOp& o = ops[pending[pi]];
+      if (!opt.lphase_table || B.idx.empty() || o.type != OP_DPHASE || o.cm == 0 ||
+          (o.cm & (o.cm - 1)) != 0 || o.cv != o.cm || popc64(B.tile | o.cm) <= k)
+        return false;
+      for (std::size_t pj = pi + 1; pj < pending.size(); pj++) {
+        const LOp& h = ops[pending[pj]];
+        if (!(h.mix() & o.cm)) continue;
+        return h.type == OP_H && h.cm == 0 && (1ull << h.g0) == o.cm;
+      }
+      return false;
+    };
+    for (std::size_t pi = 0; pi < pending.size(); pi++) {
+      const int idx = pending[pi];
       const LOp& o = ops[idx];
       uint64_t mx = o.mix(), dg = o.diag();
       bool commutes = !(mx & blocked_all) && !(dg & blocked_mix);
       bool room = (int)B.idx.size() < MAX_OPS - 1 && coefs + o.ncoef <= MAX_COEF &&
                   (o.type != OP_GRAD || grads < opt.max_grads);
-      if (commutes && room) {
+      if (commutes && room && !waits_for_h(pi)) {
         uint64_t t = B.tile | mx;
         if (popc64(t) <= k) {
           B.tile = t;

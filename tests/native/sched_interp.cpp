@@ -186,7 +186,25 @@ int main(int argc, char** argv) {
     std::vector<lq_gate> g;
     std::vector<double> p;
     auto angle = [&]() { return (double)(rng() % 20000) / 2000.0 - 5.0; };
-    if (t % 3 == 0) {   // hardware-efficient layers: RY, RZ on every qubit, CNOT ladder or ring
+    if (t % 6 == 1) {   // Alg. 3 (H, then CP(pi/2^(j-i)) from i to j > i), forward or reversed
+      std::vector<lq_gate> f;
+      for (int i = 0; i < n; i++) {
+        f.push_back(make_gate(LQ_H, i, -1, -1));
+        for (int j = i + 1; j < n; j++) {
+          lq_gate c = make_gate(LQ_CP, i, j, -1);
+          c.angle = M_PI / std::ldexp(1.0, j - i);
+          f.push_back(c);
+        }
+      }
+      if (t % 12 == 7)
+        for (int i = (int)f.size() - 1; i >= 0; i--) {
+          lq_gate c = f[i];
+          c.angle = -c.angle;
+          g.push_back(c);
+        }
+      else
+        g = f;
+    } else if (t % 3 == 0) {   // hardware-efficient layers: RY, RZ on every qubit, CNOT ladder or ring
       const int depth = 1 + (int)(rng() % 3);
       for (int l = 0; l < depth; l++) {
         for (int r = 0; r < 2; r++)
