@@ -294,8 +294,12 @@ lq_status lq_expval_plan(int n, const lq_pauli_term* terms, int nt, lq_plan_info
         } else if (G.mode == XG_TABLE) {
           fl += 2.5 * parts * N;                  // MUL + FMA, then FMA, per pair and part
         } else {
-          const int direct = X.tables ? G.first + G.count - G.direct : G.count;
-          fl += (5.0 + (X.tables ? nch : 0) + direct) * N;   // |psi|^2, d(i), FMA
+          if (X.dcls) {   // |psi|^2, the classes' table values, FMA
+            fl += (5.0 + (X.dcls - 1)) * N;
+          } else {
+            const int direct = X.tables ? G.first + G.count - G.direct : G.count;
+            fl += (5.0 + (X.tables ? nch : 0) + direct) * N;   // |psi|^2, d(i), FMA
+          }
         }
       }
       if (X.npass) tb = X.passes[0].k;

@@ -210,8 +210,77 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
         return __builtin_ctzll(z) / EXP_CHUNK_BITS == (63 - __builtin_clzll(z)) / EXP_CHUNK_BITS;
       };
       std::vector<int> order(G.t);
-      if (G.mode == XG_DIAG)
+      // diagonal group: a few distinct coefficients (the ZZ couplings of a
+      // chain) are cheaper as classes -- K - 1 adds per amplitude after a
+      // table lookup each -- than chunk lookups plus direct terms
+      std::vector<double> cls;
+      bool classes = false;
+      if (G.mode == XG_DIAG) {
+        int chunks = 0, direct = 0;
+        uint32_t used = 0;
+        for (int t : order) {
+          bool found = false;
+          for (double c : cls) found |= c == terms[t].coeff;
+          if (!found) cls.push_back(terms[t].coeff);
+          if (in_chunk(t)) {
+            const uint32_t cb = 1u << (__builtin_ctzll(terms[t].zmask) / EXP_CHUNK_BITS);
+            chunks += (used & cb) == 0;
+            used |= cb;
+          } else if (terms[t].zmask) {
+            direct++;
+          }
+        }
+        classes = (int)cls.size() <= XP_DIAG_CLASSES && (int)cls.size() - 1 < chunks + direct &&
+                  X->dcls == 0;
+      }
+      if (classes) {
+        // per class: two-bit terms (b, b + delta) and one-bit terms (b,
+        // delta 0) join a delta group while their low bit is new to it (at
+        // most XP_DIAG_DELTAS groups); the others are counted one by one and
+        // come first in the class
+        std::vector<int> sorted;
+        int at = D.first;
+        for (std::size_t c = 0; c < cls.size(); c++) {
+          std::vector<int> direct, paired;
+          int nd = 0;
+          int8_t del[XP_DIAG_DELTAS] = {0, 0};
+          uint64_t msk[XP_DIAG_DELTAS] = {0, 0};
+          for (int t : order) {
+            if (terms[t].coeff != cls[c]) continue;
+            const uint64_t z = terms[t].zmask;
+            bool joined = false;
+            if (pc64(z) == 2 || pc64(z) == 1) {   // delta 0: one-bit terms
+              const int lo = __builtin_ctzll(z), dl = 63 - __builtin_clzll(z) - lo;
+              for (int e = 0; e < nd && !joined; e++)
+                if (del[e] == dl && !(msk[e] >> lo & 1)) {
+                  msk[e] |= 1ull << lo;
+                  joined = true;
+                }
+              if (!joined && nd < XP_DIAG_DELTAS) {
+                del[nd] = (int8_t)dl;
+                msk[nd++] = 1ull << lo;
+                joined = true;
+              }
+            }
+            (joined ? paired : direct).push_back(t);
+          }
+          X->dfirst[c] = (int16_t)at;
+          X->dcount[c] = (int16_t)(direct.size() + paired.size());
+          X->ddirect[c] = (int16_t)direct.size();
+          X->dnd[c] = (int8_t)nd;
+          for (int e = 0; e < XP_DIAG_DELTAS; e++) {
+            X->ddel[c][e] = del[e];
+            X->dmsk[c][e] = msk[e];
+          }
+          at += X->dcount[c];
+          sorted.insert(sorted.end(), direct.begin(), direct.end());
+          sorted.insert(sorted.end(), paired.begin(), paired.end());
+        }
+        order.swap(sorted);
+        X->dcls = (int32_t)cls.size();
+      } else if (G.mode == XG_DIAG) {
         std::stable_partition(order.begin(), order.end(), in_chunk);
+      }
       D.direct = D.first;
       int odd = 0, even = 0;
       for (int t : order) {
@@ -227,7 +296,7 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
         }
         T.k0 = pc64(src.xmask & src.zmask) & 3;
         T.chunk = 0;
-        if (G.mode == XG_DIAG && src.zmask) {
+        if (G.mode == XG_DIAG && src.zmask && !classes) {
           const int lo = __builtin_ctzll(src.zmask), hi = 63 - __builtin_clzll(src.zmask);
           if (lo / EXP_CHUNK_BITS == hi / EXP_CHUNK_BITS) T.chunk = 1 + lo / EXP_CHUNK_BITS;
         }
@@ -382,6 +451,13 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
   double2* coef = xsm + Tmax;
   double* tab = reinterpret_cast<double*>(coef + X.ncoef);
   for (int e = tid; e < X.ncoef; e += BLOCK) coef[e] = X.coef[e];
+  if (X.dcls && X.diag >= 0) {
+    // class tables: tab[off_c + p] = coefficient_c (count_c - 2 p), p = the
+    // number of class-c terms with odd parity at an index
+    for (int c = 0, off = 0; c < X.dcls; off += X.dcount[c] + 1, c++)
+      for (int p = tid; p <= X.dcount[c]; p += BLOCK)
+        tab[off + p] = X.terms[X.dfirst[c]].c * (double)(X.dcount[c] - 2 * p);
+  }
   if (X.tables && X.diag >= 0) {
     // tab[c][v] = sum of the chunk-c diagonal terms c_t (-1)^popcount(v & z_t)
     const XGroup& G = X.groups[X.diag];
@@ -426,6 +502,26 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
             acc += xp_class_group<BLOCK, 1>(sm, T, G, coef);
           else
             acc += xp_class_group<BLOCK, 2>(sm, T, G, coef);
+        } else if (G.mode == XG_DIAG && X.dcls) {
+          // per class: count the odd parities with integer operations, read
+          // the class's sum from its table (K - 1 adds per amplitude)
+          for (uint32_t s = tid; s < T; s += BLOCK) {
+            const uint64_t gi = base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask);
+            const double2 v = sm[s];
+            const double pr = fma(v.x, v.x, v.y * v.y);
+            double d = 0.0;
+            for (int c = 0, off = 0; c < X.dcls; off += X.dcount[c] + 1, c++) {
+              int odd = 0;
+              for (int q = X.dfirst[c]; q < X.dfirst[c] + X.ddirect[c]; q++)
+                odd += __popcll(gi & X.terms[q].zg) & 1;
+              for (int e = 0; e < X.dnd[c]; e++) {
+                const int dl = X.ddel[c][e];
+                odd += __popcll((dl ? gi ^ (gi >> dl) : gi) & X.dmsk[c][e]);
+              }
+              d = c ? d + tab[off + odd] : tab[off + odd];
+            }
+            acc = fma(d, pr, acc);
+          }
         } else if (G.mode == XG_DIAG) {
           for (uint32_t s = tid; s < T; s += BLOCK) {
             const uint64_t gi = base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask);
@@ -486,8 +582,10 @@ cudaError_t launch_expval_tiled(const XPlan& X, const double2* states, uint64_t 
   (void)cudaGetLastError();  // report only this launcher's own errors
   const int k = X.npass ? X.passes[0].k : 0;
   const int nch = (X.n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS;
+  int ctab = 0;   // class tables of the diagonal group
+  for (int c = 0; c < X.dcls; c++) ctab += X.dcount[c] + 1;
   const size_t smem = (sizeof(double2) << k) + sizeof(double2) * X.ncoef +
-                      (X.tables ? sizeof(double) * 256 * nch : 0);
+                      (X.tables ? sizeof(double) * 256 * nch : 0) + sizeof(double) * ctab;
   static std::atomic<uint64_t> configured{0};
   cudaError_t ce = once_per_device(configured, [] {
     return cudaFuncSetAttribute(

@@ -74,8 +74,21 @@ struct XPass {
   int8_t tbits[16];
   int8_t obits[48];
 };
+constexpr int XP_DIAG_CLASSES = 4;   // coefficient classes of a diagonal group
+constexpr int XP_DIAG_DELTAS = 2;    // pair-term groups per class
 struct XPlan {
-  int32_t n, npass, ngroups, nterms, ncoef, tables, diag, pad;
+  int32_t n, npass, ngroups, nterms, ncoef, tables, diag;
+  // nonzero: the diagonal group's terms form dcls classes of equal
+  // coefficient, terms [dfirst[c], dfirst[c] + dcount[c]); an amplitude's
+  // class-c value c (count - 2 #odd) is read from a per-CTA table by its
+  // number of odd parities, counted with integer operations: the first
+  // ddirect[c] terms one by one, the class's two-bit terms (b, b + delta)
+  // in groups of one delta as popcount((i ^ (i >> delta)) & mask), one-bit
+  // terms as the group of delta 0, popcount(i & mask)
+  int32_t dcls;
+  int16_t dfirst[XP_DIAG_CLASSES], dcount[XP_DIAG_CLASSES], ddirect[XP_DIAG_CLASSES];
+  int8_t dnd[XP_DIAG_CLASSES], ddel[XP_DIAG_CLASSES][XP_DIAG_DELTAS];
+  uint64_t dmsk[XP_DIAG_CLASSES][XP_DIAG_DELTAS];
   XPass passes[XP_MAX_PASS];
   XGroup groups[XP_MAX_GROUPS];
   XTerm terms[XP_MAX_TERMS];
