@@ -44,6 +44,7 @@
 namespace lq {
 
 constexpr int FFT_MAX_D = 12;                     // qubits per pass
+constexpr int FFT_FULL_DIAG = 10;                 // largest group with a 2^d diagonal table
 constexpr int FFT_TABLE = (1 << FFT_MAX_D) - 1;   // sum_{r<12} 2^r entries
 
 // g_tw[(1 << r) - 1 + v]: twiddle w = exp(2 pi i u / 2^{r+1}) = exp(i pi u /
@@ -217,7 +218,11 @@ __global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F
   __shared__ double2 omega[FFT_MAX_D];
   const int k = F.k, ms = F.ms, d = F.d, plo = F.plo;
   const uint32_t T = 1u << k;
-  double2* dtab = sm + T;                  // 2^d entries after the tile
+  // the diagonal's table after the tile: 2^d entries, or (groups of more
+  // than FFT_FULL_DIAG qubits) two tables of 2^dl and 2^(d - dl)
+  const bool split = d > FFT_FULL_DIAG;
+  const int dl = d / 2;
+  double2* dtab = sm + T;
   const uint64_t ntiles = 1ull << (F.n - k);
   const int nlow = plo - ms;               // CTA bits below the group: [ms, plo)
   // sign flips for the inverse transform (conjugate twiddles), integer only
@@ -242,12 +247,28 @@ __global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F
         omega[tid] = make_double2(cs, xsign(sn, fpos));
       }
       if (tid == 0) dtab[0] = make_double2(F.scale, 0.0);
+      if (split && tid == 1) dtab[1 << dl] = make_double2(1.0, 0.0);
       __syncthreads();
-      for (int r = 0; r < d; r++) {
-        const double2 om = omega[r];
-        for (uint32_t v = tid; v < (1u << r); v += BLOCK)
-          dtab[v | (1u << r)] = cmul(dtab[v], om.x, om.y);
-        __syncthreads();
+      if (split) {
+        // D(V) = lo[V mod 2^dl] hi[V >> dl]: two tables of 2^dl and 2^(d-dl)
+        // entries (the 2^d-entry one would take as much shared memory as the
+        // tile, and cost one complex multiply per amplitude to build)
+        double2* hi = dtab + (1 << dl);
+        for (int r = 0; r < d - dl || r < dl; r++) {
+          const double2 om = omega[r], oh = omega[dl + r < d ? dl + r : 0];
+          for (uint32_t v = tid; v < (1u << r); v += BLOCK) {
+            if (r < dl) dtab[v | (1u << r)] = cmul(dtab[v], om.x, om.y);
+            if (r < d - dl) hi[v | (1u << r)] = cmul(hi[v], oh.x, oh.y);
+          }
+          __syncthreads();
+        }
+      } else {
+        for (int r = 0; r < d; r++) {
+          const double2 om = omega[r];
+          for (uint32_t v = tid; v < (1u << r); v += BLOCK)
+            dtab[v | (1u << r)] = cmul(dtab[v], om.x, om.y);
+          __syncthreads();
+        }
       }
     }
     const uint32_t lm = (1u << ms) - 1u;
@@ -256,7 +277,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F
       const uint64_t g = base | (s & lm) | ((uint64_t)(s >> ms) << plo);
       double2 v = state[g];
       if (diag) {
-        const double2 w = dtab[s >> ms];
+        const uint32_t V = s >> ms;
+        double2 w;
+        if (split) {
+          const double2 a = dtab[V & ((1u << dl) - 1u)], b = dtab[(1u << dl) + (V >> dl)];
+          w = cmul(a, b.x, b.y);
+        } else {
+          w = dtab[V];
+        }
         v = cmul(v, w.x, w.y);
       }
       sm[s] = v;
@@ -351,7 +379,9 @@ cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, 
   F.k = F.ms + F.d;
   F.inverse = inverse;
   F.scale = scale;
-  size_t smem = (sizeof(double2) << F.k) + (sizeof(double2) << F.d);
+  size_t smem = (sizeof(double2) << F.k) +
+                (F.d > FFT_FULL_DIAG ? sizeof(double2) * ((1u << (F.d / 2)) + (1u << (F.d - F.d / 2)))
+                                     : sizeof(double2) << F.d);
   int per_sm = (int)((228u << 10) / (smem + (2u << 10)));
   per_sm = per_sm < 1 ? 1 : per_sm > 4 ? 4 : per_sm;
   if (per_sm == 3) per_sm = 2;
@@ -539,8 +569,10 @@ extern "C" lq_status lq_qft_plan_dir(int n, int method, int inverse, lq_plan_inf
     // stages 22 FMA per quad (radix 4), an odd last stage 6 FMA per pair; a
     // one-stage pass 2 adds per amplitude
     fl += d == 1 ? 2.0 * N : N * (4.0 + 11.0 * ((d - 2) / 2) + 6.0 * ((d - 2) % 2));
-    // diagonal of the pass (all but the first; the last also carries the scale)
-    if (p > 0 || b.size() == 2) fl += 6.0 * N;
+    // diagonal of the pass (all but the first; the last also carries the
+    // scale): a complex multiply, and for groups read from two tables the
+    // product of the two entries
+    if (p > 0 || b.size() == 2) fl += (d > FFT_FULL_DIAG ? 12.0 : 6.0) * N;
   }
   out->npasses = (int)b.size();   // FFT passes + the bit-reversal pass
   out->tile_bits = kmax;
