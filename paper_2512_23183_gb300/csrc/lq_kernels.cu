@@ -309,10 +309,24 @@ cudaError_t launch_pass(const PassParams& P, double2* state, uint64_t stride, in
   });
   if (ce != cudaSuccess) return ce;
   uint64_t total = P.h.ntiles * (uint64_t)nstates;
-  // resident CTAs per SM: the launch bound allows 4; shared memory (dynamic
-  // + ~6 KiB static + 1 KiB reserved, of 228 KiB) may allow fewer
-  int per_sm = (int)((228u << 10) / (smem + (7u << 10)));
-  per_sm = per_sm < 1 ? 1 : per_sm > 4 ? 4 : per_sm;
+  // resident CTAs per SM (the launch bound allows 4; dynamic and static
+  // shared memory may allow fewer): a grid of more CTAs than fit would run
+  // its last CTAs as a second wave.  Four CTAs with up to 46 KiB of dynamic
+  // shared memory each always fit (static ~8 KiB and 1 KiB reserved per CTA
+  // of 228 KiB); above that the occupancy query decides (it costs
+  // microseconds, which launches on small states feel)
+  int per_sm = 4;
+  if (total > (uint64_t)sm_count() && smem > (46u << 10)) {
+    int occ = 0;
+    const bool bf = (P.h.flags & PF_DYADIC) && (P.h.flags & PF_BFLY);
+    cudaError_t oe =
+        bf ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel<kPassBlock, true>,
+                                                           kPassBlock, smem)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pass_kernel<kPassBlock, false>,
+                                                           kPassBlock, smem);
+    if (oe != cudaSuccess) return oe;
+    per_sm = occ < 1 ? 1 : occ > 4 ? 4 : occ;
+  }
   uint64_t cap = (uint64_t)sm_count() * per_sm;
   int grid = (int)(total < cap ? total : cap);
   if (P.h.flags & PF_DYADIC) {
