@@ -333,6 +333,23 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
           }
           X->coef[X->ncoef++] = C;
         }
+        // an earlier class group of this plan with the same width, part
+        // and coefficients: share its block, so that the kernel adds both
+        // groups' class sums before applying the coefficients once
+        const int nc = 1 << W;
+        for (int e = 0; e < X->ngroups - 1; e++) {
+          const XGroup& E = X->groups[e];
+          if (E.mode != XG_CLASS || E.w != D.w || E.part != D.part) continue;
+          bool same = true;
+          for (int c = 0; c < nc && same; c++)
+            same = X->coef[E.coef + c].x == X->coef[D.coef + c].x &&
+                   X->coef[E.coef + c].y == X->coef[D.coef + c].y;
+          if (same) {
+            X->ncoef -= nc;
+            D.coef = E.coef;
+            break;
+          }
+        }
       } else if (G.mode == XG_TABLE) {
         // index bit t = parity(j & z_t)
         for (int idx = 0; idx < (1 << D.count); idx++) {
@@ -358,8 +375,8 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
 // Class-mode sums over this thread's indices j of the tile (j runs over the
 // k - w bits outside x): amplitude i = expand(j) | dep[c] (lower x bits = class
 // c, top x bit clear) pairs with i ^ x; sr[c] += Re conj(psi_i) psi_{i^x},
-// si[c] += Im (as `part` asks).  Every class of an index is handled by the same
-// thread, so the index expansion is shared.
+// si[c] += Im (as `part` asks), added to what sr and si hold.  Every class of
+// an index is handled by the same thread, so the index expansion is shared.
 template <int BLOCK, int W>
 __device__ __forceinline__ void xp_class_sums(const double2* __restrict__ sm, uint32_t T,
                                               uint32_t x, int part, const uint32_t* dep,
@@ -376,8 +393,6 @@ __device__ __forceinline__ void xp_class_sums(const double2* __restrict__ sm, ui
       mk &= mk - 1;
     }
   }
-#pragma unroll
-  for (int c = 0; c < NC; c++) sr[c] = si[c] = 0.0;
   constexpr int NL = NC < 2 ? NC : 2;   // classes loaded together (register budget)
   for (uint32_t j = threadIdx.x; j < cnt; j += BLOCK) {
     uint32_t a = j;
@@ -400,31 +415,40 @@ __device__ __forceinline__ void xp_class_sums(const double2* __restrict__ sm, ui
   }
 }
 
+// A run of class groups G[0..ng) of one width, part and coefficient block
+// (the XX + YY groups of a uniform chain): their class sums add up before
+// the coefficients are applied, so the fold costs 2^w FMAs per thread and
+// tile for the whole run instead of for each group.
 template <int BLOCK, int W>
-__device__ __forceinline__ double xp_class_group(const double2* __restrict__ sm, uint32_t T,
-                                                 const XGroup& G,
-                                                 const double2* __restrict__ coef) {
+__device__ __forceinline__ double xp_class_run(const double2* __restrict__ sm, uint32_t T,
+                                               const XGroup* G, int ng,
+                                               const double2* __restrict__ coef) {
   constexpr int NC = 1 << W;
-  uint32_t dep[NC];
-  // deposit the class bits into the lower x bits (ascending)
-#pragma unroll
-  for (int c = 0; c < NC; c++) {
-    uint32_t d = 0, mk = G.x & ~(1u << G.h);
-    for (int b = 0; mk; b++) {
-      const int bit = __ffs(mk) - 1;
-      mk &= mk - 1;
-      if (c >> b & 1) d |= 1u << bit;
-    }
-    dep[c] = d;
-  }
   double sr[NC], si[NC];
-  xp_class_sums<BLOCK, W>(sm, T, G.x, G.part, dep, sr, si);
+#pragma unroll
+  for (int c = 0; c < NC; c++) sr[c] = si[c] = 0.0;
+  for (int r = 0; r < ng; r++) {
+    uint32_t dep[NC];
+    // deposit the class bits into the lower x bits (ascending)
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      uint32_t d = 0, mk = G[r].x & ~(1u << G[r].h);
+      for (int b = 0; mk; b++) {
+        const int bit = __ffs(mk) - 1;
+        mk &= mk - 1;
+        if (c >> b & 1) d |= 1u << bit;
+      }
+      dep[c] = d;
+    }
+    xp_class_sums<BLOCK, W>(sm, T, G[r].x, G[r].part, dep, sr, si);
+  }
+  const XGroup& G0 = G[0];
   double acc = 0.0;
 #pragma unroll
   for (int c = 0; c < NC; c++) {
-    const double2 C = coef[G.coef + c];
-    if (G.part != 2) acc = fma(C.x, sr[c], acc);
-    if (G.part != 1) acc = fma(C.y, si[c], acc);
+    const double2 C = coef[G0.coef + c];
+    if (G0.part != 2) acc = fma(C.x, sr[c], acc);
+    if (G0.part != 1) acc = fma(C.y, si[c], acc);
   }
   return acc;
 }
@@ -496,12 +520,18 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
       for (int g = Q.g0; g < Q.g1; g++) {
         const XGroup& G = X.groups[g];
         if (G.mode == XG_CLASS) {
+          int ng = 1;
+          while (g + ng < Q.g1 && X.groups[g + ng].mode == XG_CLASS &&
+                 X.groups[g + ng].w == G.w && X.groups[g + ng].part == G.part &&
+                 X.groups[g + ng].coef == G.coef)
+            ng++;
           if (G.w == 1)
-            acc += xp_class_group<BLOCK, 0>(sm, T, G, coef);
+            acc += xp_class_run<BLOCK, 0>(sm, T, &G, ng, coef);
           else if (G.w == 2)
-            acc += xp_class_group<BLOCK, 1>(sm, T, G, coef);
+            acc += xp_class_run<BLOCK, 1>(sm, T, &G, ng, coef);
           else
-            acc += xp_class_group<BLOCK, 2>(sm, T, G, coef);
+            acc += xp_class_run<BLOCK, 2>(sm, T, &G, ng, coef);
+          g += ng - 1;
         } else if (G.mode == XG_DIAG && X.dcls) {
           // per class: count the odd parities with integer operations, read
           // the class's sum from its table (K - 1 adds per amplitude)
@@ -509,17 +539,19 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
             const uint64_t gi = base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask);
             const double2 v = sm[s];
             const double pr = fma(v.x, v.x, v.y * v.y);
-            double d = 0.0;
-            for (int c = 0, off = 0; c < X.dcls; off += X.dcount[c] + 1, c++) {
-              int odd = 0;
+            auto odd = [&](int c) {   // class-c terms with odd parity at gi
+              int o = 0;
               for (int q = X.dfirst[c]; q < X.dfirst[c] + X.ddirect[c]; q++)
-                odd += __popcll(gi & X.terms[q].zg) & 1;
+                o += __popcll(gi & X.terms[q].zg) & 1;
               for (int e = 0; e < X.dnd[c]; e++) {
                 const int dl = X.ddel[c][e];
-                odd += __popcll((dl ? gi ^ (gi >> dl) : gi) & X.dmsk[c][e]);
+                o += __popcll((dl ? gi ^ (gi >> dl) : gi) & X.dmsk[c][e]);
               }
-              d = c ? d + tab[off + odd] : tab[off + odd];
-            }
+              return o;
+            };
+            double d = tab[odd(0)];
+            for (int c = 1, off = X.dcount[0] + 1; c < X.dcls; off += X.dcount[c] + 1, c++)
+              d += tab[off + odd(c)];
             acc = fma(d, pr, acc);
           }
         } else if (G.mode == XG_DIAG) {
