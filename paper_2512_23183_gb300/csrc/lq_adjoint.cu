@@ -273,7 +273,8 @@ __global__ void __launch_bounds__(BLOCK, 3) pass2_kernel(const __grid_constant__
         const int gA = (k0 + 2 * ((op.z_loc != 0) + zsg)) & 3, gB = (k0 + 2 * zsg) & 3;
         const int rk0 = r.mode >> 2;
         const int kA = (rk0 + 2 * ((r.z_loc != 0) + zsr)) & 3, kB = (rk0 + 2 * zsr) & 3;
-        const double a = r.a, cA = (kA & 2) ? -a : a, cB = (kB & 2) ? -a : a;
+        const double a = r.a, cA = xsign(a, (uint32_t)(kA & 2) << 30),
+                     cB = xsign(a, (uint32_t)(kB & 2) << 30);
         const uint32_t sA = (uint32_t)(kA & 2) << 30, sB = (uint32_t)(kB & 2) << 30;
         const bool odd = kA & 1;
         if ((r.mode & 3) == PM_TAN) {

@@ -44,6 +44,13 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Hint: bring the cache line holding gmem into L2 (no register result, no
+// wait).  A tile kernel issues it for its next tile while it computes the
+// current one, so that tile's synchronous load hits L2 instead of HBM.
+__device__ __forceinline__ void prefetch_l2(const void* gmem) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(gmem));
+}
+
 // Insert a zero bit at position b of j.
 __device__ __forceinline__ uint32_t insert0(uint32_t j, int b) {
   uint32_t lo = j & ((1u << b) - 1u);
@@ -497,8 +504,10 @@ __device__ __forceinline__ void apply_op(double2* __restrict__ sm, uint32_t T, c
         // uniform phases: w_A = i^kA (pairs' s1 has the Z bit), w_B = i^kB
         const int kA = (k0 + 2 * (((z != 0) + zs) & 1)) & 3;
         const int kB = (k0 + 2 * (zs & 1)) & 3;
-        const double cA = (kA & 2) ? -a : a, cB = (kB & 2) ? -a : a;
+        // the signs as sign-bit flips (a double negation would take an FP64
+        // instruction per thread and op)
         const uint32_t sA = (uint32_t)(kA & 2) << 30, sB = (uint32_t)(kB & 2) << 30;
+        const double cA = xsign(a, sA), cB = xsign(a, sB);
         const int v = ((kA & 1) << 1) | (kB & 1);
 #define LQ_ROT1(F, A_, B_) rot1_pairs<BLOCK, F, A_, B_>(sm, cnt, M, cv, x, a, cA, cB, sA, sB)
 #define LQ_ROT1_FORM(F)                      \

@@ -514,8 +514,16 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const uint64_t base = deposit(t, Q.obits, Q.nobits);
       const double2* __restrict__ sm = xsm;
-      for (uint32_t s = tid; s < T; s += BLOCK)
-        xsm[s] = st[base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask)];
+      // the next tile of this pass (same tile index, its CTA bits) into L2:
+      // one hint per run of 2^m amplitudes, at most one per 128-byte line
+      const int64_t ahead =
+          t + gridDim.x < ntiles ? (int64_t)(deposit(t + gridDim.x, Q.obits, Q.nobits) - base) : 0;
+      const uint32_t pmask = ahead ? (1u << (m < 3 ? m : 3)) - 1u : ~0u;
+      for (uint32_t s = tid; s < T; s += BLOCK) {
+        const double2* src = st + (base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask));
+        xsm[s] = *src;
+        if ((s & pmask) == 0) prefetch_l2(src + ahead);
+      }
       __syncthreads();
       for (int g = Q.g0; g < Q.g1; g++) {
         const XGroup& G = X.groups[g];

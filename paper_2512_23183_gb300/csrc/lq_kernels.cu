@@ -193,8 +193,9 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
   const bool zero = (P.h.flags & PF_INIT_ZERO) != 0;
   const bool store = !(P.h.flags & PF_NO_STORE);
   __syncthreads();
+  const int lgt = __ffsll((long long)ntiles) - 1;   // ntiles = 2^(n - k)
   auto tile_of = [&](uint64_t w, uint64_t* base) -> double2* {
-    const uint64_t si = w / ntiles, t = w - si * ntiles;
+    const uint64_t si = w >> lgt, t = w & (ntiles - 1ull);
     *base = deposit(t, P.h.obits, P.h.nobits);
     return state + si * stride;
   };
@@ -223,8 +224,21 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
         cp_async_wait<0>();
       }
     } else {
-      for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
-        sm[s] = st[base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask)];
+      // the next tile's amplitude at the same tile index lies `ahead`
+      // amplitudes further (its CTA bits replace this tile's): one L2 hint
+      // per 128-byte line (or per run of 2^m amplitudes when runs are shorter)
+      int64_t ahead = 0;
+      if (w + gridDim.x < total) {
+        uint64_t b2;
+        const double2* st2 = tile_of(w + gridDim.x, &b2);
+        ahead = (st2 + b2) - (st + base);
+      }
+      const uint32_t pmask = ahead ? (1u << (m < 3 ? m : 3)) - 1u : ~0u;
+      for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+        const double2* src = st + (base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask));
+        sm[s] = *src;
+        if ((s & pmask) == 0) prefetch_l2(src + ahead);
+      }
     }
     __syncthreads();
     if (deferred && P.h.dpre) {

@@ -128,6 +128,7 @@ cudaError_t fft_tables_init(cudaStream_t s) {
 struct FftParams {
   int n, q0, q1, d, ms, plo, k;
   int inverse;
+  int scaled;     // scale != 1 (decided on the host: no per-tile FP64 compare)
   double scale;   // folded into the diagonal (or applied alone)
 };
 
@@ -228,15 +229,22 @@ __global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F
   // sign flips for the inverse transform (conjugate twiddles), integer only
   const uint32_t fpos = F.inverse ? 0x80000000u : 0u, fneg = fpos ^ 0x80000000u;
   const uint32_t tid = threadIdx.x;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  // each CTA takes a contiguous range of tiles: M_out (the top q0 index
+  // bits) then stays the same over runs of tiles, and the diagonal's table
+  // is rebuilt only when it changes
+  const uint64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t t_end = (blockIdx.x + 1) * per < ntiles ? (blockIdx.x + 1) * per : ntiles;
+  uint64_t have = ~0ull;   // M_out of the table in dtab (none yet)
+  for (uint64_t t = blockIdx.x * per; t < t_end; t++) {
     // CTA bits: low part -> [ms, plo), high part -> [plo + d, n)
     const uint64_t tlo = t & ((1ull << nlow) - 1ull), thi = t >> nlow;
     const uint64_t base = (tlo << ms) | (thi << (plo + d));
     // M_out = sum_{q<q0} b_q 2^q over the high CTA bits: qubit q is bit n-1-q
     uint64_t mout = 0;
     for (int q = 0; q < F.q0; q++) mout |= ((base >> (F.n - 1 - q)) & 1ull) << q;
-    const bool diag = (mout != 0) || (F.scale != 1.0);
-    if (diag) {
+    const bool diag = (mout != 0) || F.scaled;
+    if (diag && mout != have) {
+      have = mout;
       // D(V) = scale * exp(sgn 2 pi i mout V / 2^{q1}), built by doubling from
       // directly evaluated factors exp(sgn 2 pi i (mout 2^r mod 2^{q1}) / 2^{q1})
       const uint64_t modmask = (F.q1 >= 64) ? ~0ull : ((1ull << F.q1) - 1ull);
@@ -272,9 +280,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) fft_pass_kernel(const FftParams F
       }
     }
     const uint32_t lm = (1u << ms) - 1u;
+    // the next tile's amplitude at the same tile index lies `ahead`
+    // amplitudes further: one L2 hint per run of 2^ms amplitudes (ms <= 3)
+    int64_t ahead = 0;
+    if (t + 1 < t_end)
+      ahead = (int64_t)((((t + 1) & ((1ull << nlow) - 1ull)) << ms) |
+                        (((t + 1) >> nlow) << (plo + d))) - (int64_t)base;
+    const uint32_t pmask = ahead ? lm : ~0u;
 #pragma unroll 4
     for (uint32_t s = tid; s < T; s += BLOCK) {
       const uint64_t g = base | (s & lm) | ((uint64_t)(s >> ms) << plo);
+      if ((s & pmask) == 0) prefetch_l2(state + g + ahead);
       double2 v = state[g];
       if (diag) {
         const uint32_t V = s >> ms;
@@ -378,6 +394,7 @@ cudaError_t launch_fft_pass(double2* state, int n, int q0, int q1, int inverse, 
   F.ms = F.plo < 3 ? F.plo : 3;   // spectator low bits for coalesced loads
   F.k = F.ms + F.d;
   F.inverse = inverse;
+  F.scaled = scale != 1.0;
   F.scale = scale;
   size_t smem = (sizeof(double2) << F.k) +
                 (F.d > FFT_FULL_DIAG ? sizeof(double2) * ((1u << (F.d / 2)) + (1u << (F.d - F.d / 2)))
