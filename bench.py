@@ -182,11 +182,18 @@ def fp64_roof(gpu_index, reps=30):
         t, m = lq.measure_fp64_fma(reps=reps)
         if t > tf:
             tf, ms = t, m
+    sw, sw_ms = lq.measure_fp64_tile_sweep(reps=5)
     clk = clocks.stop()
     return {"tflops": round(tf, 4), "ms_per_launch": round(ms, 3),
             "nominal_tflops": round(FP64_NOMINAL_TFLOPS, 4), "clocks": clk,
             "how": "lq_measure_fp64_fma: 8 independent DFMA chains per thread, 4096 FMAs each, "
-                   "every SM filled, best launch by CUDA events"}
+                   "every SM filled, best launch by CUDA events",
+            "tile_sweep_tflops": round(sw, 4), "tile_sweep_ms": round(sw_ms, 3),
+            "tile_sweep_frac_of_dfma": round(sw / tf, 4) if tf else None,
+            "tile_sweep_how": "lq_measure_fp64_tile_sweep: tangent-form rotations on a "
+                              "2^12-amplitude shared-memory tile per CTA (2 loads, 4 FMAs, "
+                              "2 stores per pair, a barrier per sweep), as many CTAs as fit "
+                              "per SM: the tile passes' access pattern without global traffic"}
 
 
 def profiled_traffic(kernel):
@@ -346,6 +353,7 @@ def bench_lq(a, rank, world, device):
     gpu_index = torch.cuda.current_device() if world == 1 else int(os.environ.get("LOCAL_RANK", 0))
     roof = fp64_roof(gpu_index)
     fp64_peak = roof["tflops"]
+    sweep = roof.get("tile_sweep_tflops")
     for _ in range(a.warmup):
         step.run()
     torch.cuda.synchronize()
@@ -388,6 +396,7 @@ def bench_lq(a, rank, world, device):
         rows[nm] = dict(ms=round(t, 3), gbs=round(r["bytes"] / (t * 1e-3) / 1e9, 1) if t else None,
                         fp64_tflops=round(tf, 4) if t else None,
                         fp64_frac=round(tf / fp64_peak, 4) if t else None,
+                        fp64_frac_of_tile_sweep=round(tf / sweep, 4) if t and sweep else None,
                         launches=r["launches"])
     # dominant kernel: the kernel family with the largest share of the step
     fam = {}
@@ -408,16 +417,19 @@ def bench_lq(a, rank, world, device):
     ach_gbs = bytes_pl / per_launch_s / 1e9
     roofline = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": round(ach_tf / fp64_peak, 4),
+                "tile_sweep_ceiling": sweep,
+                "frac_of_tile_sweep": round(ach_tf / sweep, 4) if sweep else None,
                 "traffic": profiled_traffic(dom), "kernel": dom,
                 "peak_note": "measured on this GPU in set-up (DFMA probe, fp64_roof); nominal "
                              "%.3f TFLOP/s from 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz, frac "
                              "of nominal %.4f" % (FP64_NOMINAL_TFLOPS, ach_tf / FP64_NOMINAL_TFLOPS),
                 "peak_nominal": round(FP64_NOMINAL_TFLOPS, 4),
                 "flops_note": "achieved counts the plans' flops (FMA = 2, add/multiply = 1); "
-                              "a DADD or DMUL takes an FP64 issue slot like a DFMA, so the "
-                              "FP64-pipe activity ncu measures is higher: 83-85% on the HEA "
-                              "passes, 82-83% on the gate-form QFT passes "
-                              "(profiles/pass_kernel_n24.md)",
+                              "a DADD or DMUL takes an FP64 issue slot like a DFMA; ncu counts "
+                              "exactly the planned 2 DFMA per amplitude and rotation on the HEA "
+                              "passes, at 74-85% FP64-pipe activity (profiles/fp64_mix_n24.md); "
+                              "tile_sweep_ceiling is the measured rate of the same shared-memory "
+                              "access pattern without global traffic",
                 "hbm": {"achieved_gbs": round(ach_gbs, 1), "peak_gbs": hbm_peak,
                         "frac": round(ach_gbs / hbm_peak, 4),
                         "algorithmic_bytes_per_launch": bytes_pl},

@@ -140,6 +140,16 @@ const char* lq_version(void);
  * [1, 1000] or a NULL tflops. */
 lq_status lq_measure_fp64_fma(int reps, double* tflops, double* ms_best, lq_stream stream);
 
+/* Measured FP64 rate, in TFLOP/s, of the access pattern every state-sized
+ * tile pass runs, without its global-memory traffic: each CTA (as many as
+ * fit per SM) holds a 2^12-amplitude complex128 tile in shared memory and
+ * applies tangent-form rotations (two loads, four FMAs and two stores per
+ * amplitude pair) on tile bits 0..11 in turn, 2400 sweeps with a barrier
+ * after each.  The practical ceiling of the tile kernels, beside the DFMA
+ * rate of lq_measure_fp64_fma (no paper counterpart: measurement only).
+ * Timing, arguments and errors as lq_measure_fp64_fma. */
+lq_status lq_measure_fp64_tile_sweep(int reps, double* tflops, double* ms_best, lq_stream stream);
+
 /* Parse a Pauli string (character q acts on qubit q; one of I X Y Z, length
  * n) into a term.  Host only. */
 lq_status lq_pauli_from_string(const char* s, int n, double coeff, lq_pauli_term* out);

@@ -101,6 +101,7 @@ EXPORTS = [
     "lq_vqe_adam", "lq_adjoint_plan", "lq_expval_plan", "lq_autotune_circuit",
     "lq_tune_cache_save", "lq_tune_cache_load", "lq_tune_cache_clear", "lq_tune_cache_size",
     "lq_autotune_batch", "lq_autotune_param_shift", "lq_autotune_qft", "lq_measure_fp64_fma",
+    "lq_measure_fp64_tile_sweep",
 ]
 
 
@@ -184,6 +185,7 @@ def load(build_if_missing=True):
     L.lq_tune_cache_size.argtypes = []
     L.lq_tune_cache_size.restype = ctypes.c_int
     L.lq_measure_fp64_fma.argtypes = [ctypes.c_int, P(c_double), P(c_double), c_void_p]
+    L.lq_measure_fp64_tile_sweep.argtypes = [ctypes.c_int, P(c_double), P(c_double), c_void_p]
     L.lq_adjoint_plan.argtypes = [ctypes.c_int, P(LqGate), ctypes.c_int, P(c_double), ctypes.c_int,
                                   ctypes.c_int, P(LqPlanInfo)]
     _lib = L
@@ -208,6 +210,16 @@ def measure_fp64_fma(reps=5, stream=None):
     tf, ms = c_double(), c_double()
     _check(load().lq_measure_fp64_fma(int(reps), ctypes.byref(tf), ctypes.byref(ms),
                                       _stream(stream)))
+    return tf.value, ms.value
+
+
+def measure_fp64_tile_sweep(reps=5, stream=None):
+    """Measured FP64 rate of shared-memory tile sweeps (rotations on a
+    2^12-amplitude tile, the tile passes' access pattern): (TFLOP/s, ms of the
+    best launch)."""
+    tf, ms = c_double(), c_double()
+    _check(load().lq_measure_fp64_tile_sweep(int(reps), ctypes.byref(tf), ctypes.byref(ms),
+                                             _stream(stream)))
     return tf.value, ms.value
 
 

@@ -96,6 +96,14 @@ def test_n_range_and_null_pointers(L):
     assert L.lq_expval_workspace_size(10, 3) > 0
 
 
+def test_probes_reject_bad_arguments_on_host(L):
+    tf = ctypes.c_double()
+    for fn in (L.lq_measure_fp64_fma, L.lq_measure_fp64_tile_sweep):
+        assert fn(0, ctypes.byref(tf), None, None) == 1       # reps < 1
+        assert fn(1001, ctypes.byref(tf), None, None) == 1    # reps > 1000
+        assert fn(1, None, None, None) == 1                   # no output
+
+
 def test_psr_rejects_unsupported_on_host(L):
     import paper_2512_23183_gb300 as lq
 
