@@ -291,7 +291,14 @@ void merge_dyadic(std::vector<LOp>& ops, int n, bool full_tables) {
     // control bit) one complex multiply per affected amplitude, else two
     double merged = op_flops(m, n);
     if (full_tables && cm) merged *= 0.5;
-    if (j - i >= 2 && m.ncoef <= MAX_COEF / 2 && merged < separate) {
+    // followed by the H on its one common condition bit, a merged op runs as
+    // a butterfly with that H on large states (6 FMAs per pair for both, vs
+    // 4 adds for the H and a complex multiply per factor on a quarter of the
+    // pairs): take it from two factors on
+    const bool before_h = full_tables && n >= 24 && j < ops.size() && ops[j].type == OP_H &&
+                          ops[j].cm == 0 && cm != 0 && (cm & (cm - 1)) == 0 && cv == cm &&
+                          ops[j].g0 == __builtin_ctzll(cm);
+    if (j - i >= 2 && m.ncoef <= MAX_COEF / 2 && (merged < separate || before_h)) {
       out.push_back(m);
     } else {
       for (std::size_t k = i; k < j; k++) out.push_back(ops[k]);
@@ -1049,10 +1056,22 @@ lq_status schedule_ops(int n, const LOp* ops, std::size_t nops, double zr, doubl
       s.mode = (uint8_t)((zi == 0.0 ? 1 : 0) | 2);
       s.a = zr;
       s.b = zi;
-      fill_op(P.ops[cnt], s, B.tile, pos, 0);
-      out.op_src[p * MAX_OPS + cnt] = -1;
       plist.push_back(s);
-      cnt++;
+      if ((P.h.flags & PF_DFULL) && P.h.ndefer > 0 && !opt.force_scale &&
+          coef_at + 2 <= MAX_COEF) {
+        // every amplitude of the pass is multiplied by an entry of its
+        // deferred phase table: the scalar joins those entries (a complex
+        // multiply per entry and tile) instead of costing a sweep
+        P.h.flags |= PF_DSCALE;
+        P.h.dsc = (uint16_t)coef_at;
+        P.coef[coef_at] = zr;
+        P.coef[coef_at + 1] = zi;
+        coef_at += 2;
+      } else {
+        fill_op(P.ops[cnt], s, B.tile, pos, 0);
+        out.op_src[p * MAX_OPS + cnt] = -1;
+        cnt++;
+      }
     }
     P.h.nops = cnt;
     out.pass_ops.push_back(plist);

@@ -121,6 +121,8 @@ struct PassHeader {
   uint8_t dmask[8], dval[8];   // per deferred sum: condition over the index bits
   uint8_t dpre;           // deferred sums applied after the load (bit per slot);
                           // the others are applied at the store
+  uint16_t dsc;           // PF_DSCALE: coef[dsc], coef[dsc + 1] = the circuit's
+                          // final scalar (re, im)
   uint64_t ntiles;        // 2^(n-k)
   const void* dtab;       // dyadic phase tables (device), set at launch
   int8_t tbits[16];       // tile-local bit j -> global bit position
@@ -137,6 +139,9 @@ enum PassFlags : int32_t {
                           // OP_H after them (DP_BFLY; pass_kernel's butterfly variant)
   PF_DFULL = 32,          // some table-mode OP_DPHASE ops use full phase tables and
                           // defer their per-tile phases to the store (pass_kernel only)
+  PF_DSCALE = 128,        // the circuit's final scalar (coef[dsc..]) is a factor of every
+                          // entry of the deferred phase table applied after the load
+                          // (dpre != 0) or else at the store, instead of an OP_SCALE
 };
 
 // OP_DPHASE in table mode (Op::mode bit): every factor has at most one tile

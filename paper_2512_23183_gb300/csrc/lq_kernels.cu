@@ -124,16 +124,21 @@ const double2* dyadic_tables(cudaError_t* err, const cudaStream_t* caller) {
 // every tile.
 // Deferred per-tile phase table of a pass: dD[v] = exp(2 pi i E(v) / 2^34),
 // E(v) = sum of the deferred sums (the pre-load ones, or the store ones) whose
-// conditions the index-bit pattern v meets.  No barrier.
+// conditions the index-bit pattern v meets; with PF_DSCALE, times the
+// circuit's final scalar in the table applied first (the pre-load one when
+// the pass has one).  No barrier.
 template <int BLOCK>
 __device__ __forceinline__ void build_deferred(double2* dD, const PassHeader& h,
+                                               const double* __restrict__ coef,
                                                const unsigned long long* dfe, bool pre) {
   const unsigned long long M34 = (1ull << DYADIC_BITS) - 1ull;
+  const bool scaled = (h.flags & PF_DSCALE) && (pre || h.dpre == 0);
   for (uint32_t v = threadIdx.x; v < (1u << h.ndbits); v += BLOCK) {
     unsigned long long E = 0;
     for (int q = 0; q < h.ndefer; q++)
       if ((((h.dpre >> q) & 1) != 0) == pre && (v & h.dmask[q]) == h.dval[q]) E += dfe[q];
-    dD[v] = dyadic_phase(E & M34, (const double2*)h.dtab);
+    const double2 w = dyadic_phase(E & M34, (const double2*)h.dtab);
+    dD[v] = scaled ? cmul(w, coef[h.dsc], coef[h.dsc + 1]) : w;
   }
 }
 
@@ -212,7 +217,31 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
     double2* __restrict__ sm = smem_tiles + (dbuf ? cur * T : 0);
     uint64_t base;
     double2* __restrict__ st = tile_of(w, &base);
-    if (threadIdx.x < 8) dfe[threadIdx.x] = 0;
+    // deferred sums applied after the load: they depend on the tile's CTA
+    // bits alone, so their table is built before the load and applied to the
+    // amplitudes as they arrive (a plain load; with zero-initialised tiles
+    // and cp.async buffers, in a sweep after it)
+    const bool pre = deferred && P.h.dpre;
+    const bool pre_at_load = pre && !zero && !dbuf;
+    if (threadIdx.x < 8 && !((P.h.dpre >> threadIdx.x) & 1u)) dfe[threadIdx.x] = 0;
+    if (pre) {
+      // per-tile parts hoisted to the load: warp w sums the (w mod 8)-th such
+      // ops (0 where the op's CTA condition fails)
+      int wi = 0;
+      for (int o = 0; o < nops; o++) {
+        const Op& d = P.ops[o];
+        if (d.type != OP_DPHASE || !(d.mode & DP_PRE)) continue;
+        if ((int)(threadIdx.x >> 5) == (wi++ % (BLOCK / 32))) {
+          const unsigned long long e0 = (base & d.cm_glob) == d.cv_glob
+                                            ? dphase_tile_sum(tabs.dpt + d.z_loc, (int)d.b1, base)
+                                            : 0ull;
+          if ((threadIdx.x & 31) == 0) dfe[d.b0] = e0;
+        }
+      }
+      __syncthreads();
+      build_deferred<BLOCK>(dD, P.h, P.coef, dfe, true);
+      __syncthreads();
+    }
     if (zero) {
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
         sm[s] = make_double2((base == 0 && s == 0) ? 1.0 : 0.0, 0.0);
@@ -234,28 +263,26 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
         ahead = (st2 + b2) - (st + base);
       }
       const uint32_t pmask = ahead ? (1u << (m < 3 ? m : 3)) - 1u : ~0u;
-      for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
-        const double2* src = st + (base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask));
-        sm[s] = *src;
-        if ((s & pmask) == 0) prefetch_l2(src + ahead);
+      if (pre_at_load) {
+        const int nb = P.h.ndbits;
+        for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+          const double2* src = st + (base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask));
+          uint32_t idx = 0;
+          for (int i = 0; i < nb; i++) idx |= ((s >> P.h.dbits[i]) & 1u) << i;
+          const double2 v = *src, wd = dD[idx];
+          if ((s & pmask) == 0) prefetch_l2(src + ahead);
+          sm[s] = cmul(v, wd.x, wd.y);
+        }
+      } else {
+        for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+          const double2* src = st + (base | ((uint64_t)hioff[s >> m] << m) | (s & lowmask));
+          sm[s] = *src;
+          if ((s & pmask) == 0) prefetch_l2(src + ahead);
+        }
       }
     }
     __syncthreads();
-    if (deferred && P.h.dpre) {
-      // per-tile parts hoisted to the load: warp w sums the (w mod 8)-th such ops
-      int wi = 0;
-      for (int o = 0; o < nops; o++) {
-        const Op& d = P.ops[o];
-        if (d.type != OP_DPHASE || !(d.mode & DP_PRE)) continue;
-        if ((int)(threadIdx.x >> 5) == (wi++ % (BLOCK / 32)) &&
-            (base & d.cm_glob) == d.cv_glob) {
-          const unsigned long long e0 = dphase_tile_sum(tabs.dpt + d.z_loc, (int)d.b1, base);
-          if ((threadIdx.x & 31) == 0) dfe[d.b0] = e0;
-        }
-      }
-      __syncthreads();
-      build_deferred<BLOCK>(dD, P.h, dfe, true);
-      __syncthreads();
+    if (pre && !pre_at_load) {
       const int nb = P.h.ndbits;
       for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
         uint32_t idx = 0;
@@ -278,7 +305,7 @@ __global__ void __launch_bounds__(BLOCK, 4) pass_kernel(const __grid_constant__ 
       __syncthreads();
     }
     if (post) {
-      build_deferred<BLOCK>(dD, P.h, dfe, false);
+      build_deferred<BLOCK>(dD, P.h, P.coef, dfe, false);
       __syncthreads();
     }
     if (store) {
