@@ -251,6 +251,16 @@ lq_status lq_state_init(void* amps, int n, uint64_t basis, lq_stream stream) {
 
 lq_status lq_apply_circuit(void* amps, int n, const lq_gate* gates, int ng,
                            const double* params, int np, lq_stream stream) {
+  return apply_circuit_with(amps, n, gates, ng, params, np, stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace lq {
+
+lq_status apply_circuit_with(void* amps, int n, const lq_gate* gates, int ng,
+                             const double* params, int np, lq_stream stream,
+                             const ScheduleOptions* fallback) {
   lq_status st = check_n(n);
   if (st) return st;
   if (!amps) return fail(LQ_ERR_INVALID_ARG, "amps is NULL");
@@ -259,15 +269,24 @@ lq_status lq_apply_circuit(void* amps, int n, const lq_gate* gates, int ng,
   double zr, zi;
   st = lower_circuit(n, gates, ng, params, np, &ops, &nops, &zr, &zi, true);
   if (st) return st;
-  // the autotuner's choice for this (GPU, n, circuit structure), if any
+  // the autotuner's choice for this (GPU, n, circuit structure), if any,
+  // else the caller's default
   ScheduleOptions tuned;
   tuned.lphase_table = true;
-  const bool has = tuned_options(n, gates, ng, &tuned);
+  bool has = tuned_options(n, gates, ng, &tuned);
+  if (!has && fallback) {
+    tuned = *fallback;
+    has = true;
+  }
   st = run_ops((double2*)amps, 0, 1, n, ops, nops, zr, zi, false, (cudaStream_t)stream,
                has ? &tuned : nullptr);
   delete[] ops;
   return st;
 }
+
+}  // namespace lq
+
+extern "C" {
 
 lq_status lq_expval_plan(int n, const lq_pauli_term* terms, int nt, lq_plan_info* out) {
   lq_status st = check_n(n);
@@ -321,6 +340,15 @@ lq_status lq_expval_plan(int n, const lq_pauli_term* terms, int nt, lq_plan_info
 
 lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* params, int np,
                           lq_plan_info* out) {
+  return circuit_plan_with(n, gates, ng, params, np, out, nullptr);
+}
+
+}  // extern "C"
+
+namespace lq {
+
+lq_status circuit_plan_with(int n, const lq_gate* gates, int ng, const double* params, int np,
+                            lq_plan_info* out, const ScheduleOptions* fallback) {
   lq_status st = check_n(n);
   if (st) return st;
   if (!out) return fail(LQ_ERR_INVALID_ARG, "out is NULL");
@@ -331,7 +359,8 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
   if (st) return st;
   ScheduleOptions opt;
   opt.lphase_table = true;   // run by pass_kernel
-  tuned_options(n, gates, ng, &opt);   // the schedule lq_apply_circuit would use
+  // the schedule apply_circuit_with would use
+  if (!tuned_options(n, gates, ng, &opt) && fallback) opt = *fallback;
   opt.max_hi = PASS_HI_BITS;
   opt.sink_phases = true;
   Schedule S;
@@ -365,6 +394,10 @@ lq_status lq_circuit_plan(int n, const lq_gate* gates, int ng, const double* par
   out->dram_bytes = 32.0 * std::ldexp(1.0, n) * S.npasses;
   return LQ_OK;
 }
+
+}  // namespace lq
+
+extern "C" {
 
 size_t lq_expval_workspace_size(int n, int nt) {
   (void)nt;

@@ -313,6 +313,14 @@ double op_flops(const LOp& o, int n);
 // The autotuner's schedule options for this circuit structure on the current
 // GPU (lq_tune.cu); false (opt untouched) when it has not been tuned.
 bool tuned_options(int n, const lq_gate* gates, int ng, ScheduleOptions* opt);
+
+// lq_apply_circuit and lq_circuit_plan with a default schedule for when the
+// tune cache has no entry for the circuit (nullptr: the library default).
+lq_status apply_circuit_with(void* amps, int n, const lq_gate* gates, int ng,
+                             const double* params, int np, lq_stream stream,
+                             const ScheduleOptions* fallback);
+lq_status circuit_plan_with(int n, const lq_gate* gates, int ng, const double* params, int np,
+                            lq_plan_info* out, const ScheduleOptions* fallback);
 // Structure hash of a circuit (n; per gate kind, qubits, whether it takes a
 // parameter, fixed angle / matrix) and the autotuner's batch entries.
 uint64_t circuit_structure_hash(int n, const lq_gate* gates, int ng);

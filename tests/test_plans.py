@@ -47,12 +47,19 @@ def test_xyz_chain_expval_reads(n, reads):
 
 
 def test_inverse_gate_qft_default_schedule_n30():
-    # the phases need no tile bits; the 30 H do: with k = 10 and 5 fixed low
-    # bits, 5 + 5 + 5 + 5 + 10 qubits in 5 passes, then the bit reversal
+    # the phases need no tile bits; the 30 H do: the gate form's default on
+    # large states, 2^11-amplitude tiles with 6 fixed low bits, takes
+    # 11 + 5 + 5 + 5 + 4 qubits in 5 passes, then the bit reversal
     n = 30
     p = lq.qft_plan(n, lq.QFT_GATES, inverse=True)
-    assert p["tile_bits"] == 10 and p["npasses"] == 5 + 1
+    assert p["tile_bits"] == 11 and p["npasses"] == 5 + 1
     assert p["dram_bytes"] == 6 * 32 * 2.0 ** n
+
+
+def test_gate_qft_small_states_keep_the_library_schedule():
+    # below 24 qubits the gate form keeps the library default (2^10 tiles)
+    p = lq.qft_plan(20, lq.QFT_GATES)
+    assert p["tile_bits"] == 10
 
 
 @pytest.mark.parametrize("n,masks,diag", [(12, 240, 5), (14, 400, 0), (12, 20, 300)])
