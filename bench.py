@@ -79,6 +79,9 @@ def parse():
                     help="requests of the serving measurement (Poisson pass)")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving measurement and print its JSON")
+    ap.add_argument("--psr-batched-only", action="store_true",
+                    help="run only the n=16 depth-8 ring batched parameter-shift gradient "
+                         "(--steps timed runs after one untimed) and print its JSON")
     return ap.parse_args()
 
 
@@ -536,6 +539,31 @@ def e2e(step, a):
 
 # ------------------------------------------------------- side measurements
 
+def psr_batched_only(device, steps):
+    """The n=16 depth-8 ring batched parameter-shift gradient alone (one
+    untimed run, then `steps` host-timed runs): the problem of vqe_extras'
+    vqe_n16_d8_ring_256p row, for profiling its persistent launch."""
+    import torch
+
+    import paper_2512_23183_gb300 as lq
+    import workloads as W
+
+    n = 16
+    gates, th, terms = W.vqe_ring(16, 8, 3)
+    ws = torch.empty(lq.load().lq_param_shift_workspace_size(n, len(th), len(terms),
+                                                             lq.PSR_BATCHED),
+                     dtype=torch.uint8, device=device)
+    lq.param_shift_grad(n, gates, th, terms, method=lq.PSR_BATCHED, workspace=ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e, _g = lq.param_shift_grad(n, gates, th, terms, method=lq.PSR_BATCHED, workspace=ws)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / max(steps, 1)
+    return {"ms": round(dt * 1e3, 3), "grads_per_s": round(1.0 / dt, 3), "energy": e,
+            "circuits": 2 * len(th) + 1}
+
+
 def vqe_extras(device):
     """Gradients per second, plain (per-circuit library calls) vs batched vs
     adjoint, on the n=10 depth-4 ladder problem and the n=16 depth-8 ring
@@ -890,6 +918,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
     device = "cuda:%d" % local
+    if a.psr_batched_only:
+        if rank == 0:
+            print(json.dumps({"psr_batched_n16": psr_batched_only(device, a.steps)}), flush=True)
+        return
     if a.serve_only:
         if rank == 0:
             import paper_2512_23183_gb300 as lq

@@ -30,6 +30,7 @@
 #include "lq_device.cuh"
 #include "lq_internal.h"
 #include "lq_kernels.h"
+#include "lq_xplan.cuh"
 
 namespace lq {
 
@@ -58,7 +59,7 @@ struct BProb {
   int32_t n, k, npasses, pass_first;
   int32_t ngroups, group_first;
   int32_t circ_first, ncirc;
-  int32_t tables, pad2;
+  int32_t tables, xplan;        // xplan: index of its tiled <H> plan, or -1
   int32_t np, out_first;
   int32_t comb_first, pad;
 };
@@ -80,9 +81,12 @@ struct BatchArgs {
   double* E;                   // per circuit
   double* out;                 // per problem: E, grad[np]
   int32_t* counters;           // [0] next item, [1] finished CTAs
+  const XPlan* xplans;         // tiled <H> plans (BProb::xplan)
   double2* scratch;            // per-CTA scratch states
   uint64_t scratch_stride;     // amplitudes
   int32_t nitems, nprobs;
+  uint32_t tile_amps;          // amplitudes of the shared-memory tile area; the
+                               // <H> tables follow it
 };
 
 template <int BLOCK>
@@ -132,11 +136,14 @@ __device__ __forceinline__ Op patched(const Op& src, const Patch& pt) {
 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__ BatchArgs A) {
+  // dynamic shared memory: the tile area (a whole small state or one tile of
+  // a scratch state), then the <H> tables of the problem being run
   extern __shared__ double2 sm[];
   __shared__ uint64_t hioff[256];
+  __shared__ uint32_t xhlo[32], xhhi[1 << (XP_TILE_BITS - XP_LOW_BITS - 5)];
   __shared__ double red[BLOCK / 32];
-  __shared__ double etab[((34 + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS) * 256];
   __shared__ int s_item, s_last;
+  double* etab = reinterpret_cast<double*>(sm + A.tile_amps);
   double2* __restrict__ scratch = A.scratch + (uint64_t)blockIdx.x * A.scratch_stride;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(&A.counters[0], 1);
@@ -181,8 +188,17 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
             for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
               sm[s] = make_double2((base == 0 && s == 0) ? 1.0 : 0.0, 0.0);
           } else {
-            for (uint32_t s = threadIdx.x; s < T; s += BLOCK)
-              sm[s] = scratch[base | hioff[s >> m] | (s & lowmask)];
+            // the next tile of this pass (same tile index, its CTA bits) into
+            // L2: one hint per run of 2^m amplitudes, at most one per line
+            const int64_t ahead =
+                t + 1 < B.h.ntiles
+                    ? (int64_t)(deposit(t + 1, B.h.obits, B.h.nobits) - base) : 0;
+            const uint32_t pmask = ahead ? (1u << (m < 3 ? m : 3)) - 1u : ~0u;
+            for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+              const double2* src = scratch + (base | hioff[s >> m] | (s & lowmask));
+              sm[s] = *src;
+              if ((s & pmask) == 0) prefetch_l2(src + ahead);
+            }
           }
           __syncthreads();
           for (int o = 0; o < B.h.nops; o++) {
@@ -196,8 +212,41 @@ __global__ void __launch_bounds__(BLOCK, 3) batch_kernel(const __grid_constant__
           __syncthreads();
         }
       }
-      e = expval_block<BLOCK>(scratch, n, A.groups + P.group_first, P.ngroups, A.terms, red,
-                              etab, P.tables);
+      if (P.xplan >= 0) {
+        // tiled <H> plan: its passes over the scratch state's tiles
+        const XPlan& X = A.xplans[P.xplan];
+        xp_tables<BLOCK>(X, etab);
+        double acc = 0.0;
+        for (int q = 0; q < X.npass; q++) {
+          const XPass& Q = X.passes[q];
+          const int m = Q.m;
+          const uint32_t T = 1u << Q.k, lowmask = (1u << m) - 1u;
+          __syncthreads();
+          xp_offsets(Q, xhlo, xhhi);
+          __syncthreads();
+          const uint64_t ntiles = 1ull << (n - Q.k);
+          for (uint64_t t = 0; t < ntiles; t++) {
+            const uint64_t base = deposit(t, Q.obits, Q.nobits);
+            const int64_t ahead =
+                t + 1 < ntiles ? (int64_t)(deposit(t + 1, Q.obits, Q.nobits) - base) : 0;
+            const uint32_t pmask = ahead ? (1u << (m < 3 ? m : 3)) - 1u : ~0u;
+            for (uint32_t s = threadIdx.x; s < T; s += BLOCK) {
+              const double2* src =
+                  scratch + (base | ((uint64_t)(xhlo[(s >> m) & 31u] | xhhi[(s >> m) >> 5]) << m) |
+                             (s & lowmask));
+              sm[s] = *src;
+              if ((s & pmask) == 0) prefetch_l2(src + ahead);
+            }
+            __syncthreads();
+            acc += xp_tile<BLOCK>(sm, T, X, Q, base, xhlo, xhhi, X.coef, etab);
+            __syncthreads();
+          }
+        }
+        e = block_sum<BLOCK>(acc, red);
+      } else {
+        e = expval_block<BLOCK>(scratch, n, A.groups + P.group_first, P.ngroups, A.terms, red,
+                                etab, P.tables);
+      }
     }
     if (threadIdx.x == 0) A.E[c] = e;
   }
@@ -334,9 +383,20 @@ struct BatchPlan {
   std::vector<Patch> patches;
   std::vector<int32_t> circ_prob, items, comb_first, comb_count, comb_circ;
   std::vector<double> comb_w;
+  std::vector<XPlan> xplans;
   int kmax = 0, nmax_scratch = 0, nout = 0;
+  int etab_words = 0;   // doubles of <H> tables after the tile area
   std::size_t program_bytes = 0;
 };
+
+// The largest <H> table area a launch reserves: chunk tables of a 34-qubit
+// diagonal group (class tables of a plan are smaller).
+constexpr int BATCH_MAX_TABLE_WORDS = 256 * ((34 + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS);
+
+// Dynamic shared memory of a launch: the tile area and the <H> tables.
+static std::size_t batch_smem(const BatchPlan& B) {
+  return (sizeof(double2) << B.kmax) + sizeof(double) * (std::size_t)B.etab_words;
+}
 
 static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B,
                             int tile_bits = BATCH_TILE_BITS) {
@@ -355,6 +415,11 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B,
     // one-bit phases of parametrised gates merge too: a shifted circuit's
     // patch replaces its gate's factor when the kernel builds the tables
     opt.merge_params = true;
+    // phases move to fewer merge points (each factor keeps its gate, so the
+    // patch still finds it); the schedule is built once per problem, so the
+    // host time of the search does not count against small states
+    opt.sink_phases = true;
+    opt.sink_min_qubits = 0;
     Schedule S;
     st = schedule_ops(n, ops, nops, zr, zi, opt, S);
     double flops = 0;
@@ -407,6 +472,22 @@ static lq_status plan_batch(const std::vector<HostProblem>& hps, BatchPlan& B,
     }
     P.ngroups = (int)B.groups.size() - P.group_first;
     for (int c = 0; c < got; c++) P.tables |= ch[c].tables;
+    // a state wider than the tile area takes the tiled <H> plan when its
+    // terms fit one plan (else the per-group sweeps of expval_block)
+    P.xplan = -1;
+    int words = P.tables ? 256 * ((n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS) : 0;
+    if (n > P.k && hp.nt > 0) {
+      std::vector<XPlan> xp;
+      std::vector<lq_pauli_term> wide;
+      const int kt = P.k < XP_TILE_BITS ? P.k : XP_TILE_BITS;
+      if (build_xplans(n, hp.terms, hp.nt, kt, xp, wide) == 1 && wide.empty() &&
+          xp_table_words(xp[0]) <= BATCH_MAX_TABLE_WORDS) {
+        P.xplan = (int)B.xplans.size();
+        B.xplans.push_back(xp[0]);
+        words = xp_table_words(xp[0]);
+      }
+    }
+    B.etab_words = std::max(B.etab_words, words);
     P.circ_first = (int)B.patches.size();
     P.ncirc = (int)hp.patches.size();
     P.np = hp.np;
@@ -461,9 +542,35 @@ static std::size_t scratch_budget() {
   return cached[dev];
 }
 
+// The kernel's shared-memory limit: the largest tile area and table area.
+static cudaError_t configure_batch_kernel() {
+  static std::atomic<uint64_t> configured{0};
+  return once_per_device(configured, [] {
+    return cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)((sizeof(double2) << BATCH_SMEM_BITS) +
+                                      sizeof(double) * BATCH_MAX_TABLE_WORDS));
+  });
+}
+
 static int batch_grid(const BatchPlan& B) {
-  std::size_t smem = sizeof(double2) << B.kmax;
-  int per_sm = smem <= 16384 ? 6 : smem <= 32768 ? 4 : smem <= 65536 ? 3 : 1;
+  const std::size_t smem = batch_smem(B);
+  // resident CTAs per SM from the occupancy query (registers, static and
+  // dynamic shared memory); without a device, an estimate from shared memory
+  static const bool have_device = [] {
+    int c = 0;
+    const bool ok = cudaGetDeviceCount(&c) == cudaSuccess && c > 0;
+    (void)cudaGetLastError();
+    return ok;
+  }();
+  int per_sm = 0;
+  if (!have_device || configure_batch_kernel() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<256>, 256, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    per_sm = (int)((228u << 10) / (smem + (8u << 10)));
+    per_sm = per_sm < 1 ? 1 : per_sm > 3 ? 3 : per_sm;
+  }
   int g = sm_count() * per_sm;
   if ((int)B.items.size() < g) g = (int)B.items.size();
   if (B.nmax_scratch > 0) {
@@ -485,7 +592,8 @@ static std::size_t batch_bytes(const BatchPlan& B, int grid) {
   std::size_t b = 0;
   b += vbytes(B.probs) + vbytes(B.passes) + vbytes(B.ops) + vbytes(B.coef) + vbytes(B.groups) +
        vbytes(B.terms) + vbytes(B.patches) + vbytes(B.circ_prob) + vbytes(B.items) +
-       vbytes(B.comb_first) + vbytes(B.comb_count) + vbytes(B.comb_circ) + vbytes(B.comb_w);
+       vbytes(B.comb_first) + vbytes(B.comb_count) + vbytes(B.comb_circ) + vbytes(B.comb_w) +
+       vbytes(B.xplans);
   b += align256(sizeof(double) * B.patches.size());   // E
   b += align256(sizeof(double) * (std::size_t)B.nout); // out
   b += align256(sizeof(int32_t) * 2);                  // counters
@@ -592,6 +700,7 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
   LQ_PLACE(B.comb_count, comb_count, const int32_t*);
   LQ_PLACE(B.comb_circ, comb_circ, const int32_t*);
   LQ_PLACE(B.comb_w, comb_w, const double*);
+  LQ_PLACE(B.xplans, xplans, const XPlan*);
 #undef LQ_PLACE
   const std::size_t image = off;
   A.E = (double*)(p + off);
@@ -604,7 +713,8 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
   A.scratch_stride = B.nmax_scratch > 0 ? (1ull << B.nmax_scratch) : 0;
   A.nitems = (int)B.items.size();
   A.nprobs = (int)B.probs.size();
-  const std::size_t smem = sizeof(double2) << B.kmax;
+  A.tile_amps = 1u << B.kmax;
+  const std::size_t smem = batch_smem(B);
   key.push_back(B.patches.size());
   key.push_back((std::size_t)B.nout);
   key.push_back((std::size_t)grid);
@@ -615,11 +725,7 @@ static lq_status run_batch(const BatchPlan& B, void* workspace, std::size_t ws_b
   int dev = 0;
   LQ_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(LQ_ERR_INVALID_ARG, "device %d", dev);
-  static std::atomic<uint64_t> configured{0};
-  LQ_CUDA(once_per_device(configured, [] {
-    return cudaFuncSetAttribute(batch_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double2) << BATCH_SMEM_BITS));
-  }));
+  LQ_CUDA(configure_batch_kernel());
   std::lock_guard<std::mutex> lock(g_graph_mu);
   if (!g_graph_stream[dev]) {
     LQ_CUDA(cudaStreamCreateWithFlags(&g_graph_stream[dev], cudaStreamNonBlocking));

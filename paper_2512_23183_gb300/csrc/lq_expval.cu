@@ -34,6 +34,7 @@
 #include "lq_device.cuh"
 #include "lq_internal.h"
 #include "lq_kernels.h"
+#include "lq_xplan.cuh"
 
 namespace lq {
 
@@ -372,87 +373,6 @@ int build_xplans(int n, const lq_pauli_term* terms, int nt, int kt, std::vector<
 
 // ---------------------------------------------------------------- kernel
 
-// Class-mode sums over this thread's indices j of the tile (j runs over the
-// k - w bits outside x): amplitude i = expand(j) | dep[c] (lower x bits = class
-// c, top x bit clear) pairs with i ^ x; sr[c] += Re conj(psi_i) psi_{i^x},
-// si[c] += Im (as `part` asks), added to what sr and si hold.  Every class of
-// an index is handled by the same thread, so the index expansion is shared.
-template <int BLOCK, int W>
-__device__ __forceinline__ void xp_class_sums(const double2* __restrict__ sm, uint32_t T,
-                                              uint32_t x, int part, const uint32_t* dep,
-                                              double* sr, double* si) {
-  constexpr int NC = 1 << W;
-  const uint32_t cnt = T >> (W + 1);
-  // the x bit positions, ascending (zero bits are inserted lowest first)
-  int pos[W + 1];
-  {
-    uint32_t mk = x;
-#pragma unroll
-    for (int b = 0; b <= W; b++) {
-      pos[b] = __ffs(mk) - 1;
-      mk &= mk - 1;
-    }
-  }
-  constexpr int NL = NC < 2 ? NC : 2;   // classes loaded together (register budget)
-  for (uint32_t j = threadIdx.x; j < cnt; j += BLOCK) {
-    uint32_t a = j;
-#pragma unroll
-    for (int b = 0; b <= W; b++) a = insert0(a, pos[b]);
-#pragma unroll
-    for (int c0 = 0; c0 < NC; c0 += NL) {
-      double2 A[NL], B[NL];
-#pragma unroll
-      for (int c = 0; c < NL; c++) {
-        A[c] = sm[a | dep[c0 + c]];
-        B[c] = sm[(a | dep[c0 + c]) ^ x];
-      }
-#pragma unroll
-      for (int c = 0; c < NL; c++) {
-        if (part != 2) sr[c0 + c] = fma(A[c].y, B[c].y, fma(A[c].x, B[c].x, sr[c0 + c]));
-        if (part != 1) si[c0 + c] = fma(-A[c].y, B[c].x, fma(A[c].x, B[c].y, si[c0 + c]));
-      }
-    }
-  }
-}
-
-// A run of class groups G[0..ng) of one width, part and coefficient block
-// (the XX + YY groups of a uniform chain): their class sums add up before
-// the coefficients are applied, so the fold costs 2^w FMAs per thread and
-// tile for the whole run instead of for each group.
-template <int BLOCK, int W>
-__device__ __forceinline__ double xp_class_run(const double2* __restrict__ sm, uint32_t T,
-                                               const XGroup* G, int ng,
-                                               const double2* __restrict__ coef) {
-  constexpr int NC = 1 << W;
-  double sr[NC], si[NC];
-#pragma unroll
-  for (int c = 0; c < NC; c++) sr[c] = si[c] = 0.0;
-  for (int r = 0; r < ng; r++) {
-    uint32_t dep[NC];
-    // deposit the class bits into the lower x bits (ascending)
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-      uint32_t d = 0, mk = G[r].x & ~(1u << G[r].h);
-      for (int b = 0; mk; b++) {
-        const int bit = __ffs(mk) - 1;
-        mk &= mk - 1;
-        if (c >> b & 1) d |= 1u << bit;
-      }
-      dep[c] = d;
-    }
-    xp_class_sums<BLOCK, W>(sm, T, G[r].x, G[r].part, dep, sr, si);
-  }
-  const XGroup& G0 = G[0];
-  double acc = 0.0;
-#pragma unroll
-  for (int c = 0; c < NC; c++) {
-    const double2 C = coef[G0.coef + c];
-    if (G0.part != 2) acc = fma(C.x, sr[c], acc);
-    if (G0.part != 1) acc = fma(C.y, si[c], acc);
-  }
-  return acc;
-}
-
 // One CTA walks the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... of every
 // pass of the plan (state blockIdx.y) and writes its partial sum.
 template <int BLOCK>
@@ -470,137 +390,35 @@ __global__ void __launch_bounds__(BLOCK, 4) expval_tile_kernel(const __grid_cons
   const uint32_t tid = threadIdx.x;
   const double2* __restrict__ st = states + blockIdx.y * stride;
   const int n = X.n;
-  const int nch = (n + EXP_CHUNK_BITS - 1) / EXP_CHUNK_BITS;
   const uint32_t Tmax = X.npass ? 1u << X.passes[0].k : 0u;
   double2* coef = xsm + Tmax;
   double* tab = reinterpret_cast<double*>(coef + X.ncoef);
   for (int e = tid; e < X.ncoef; e += BLOCK) coef[e] = X.coef[e];
-  if (X.dcls && X.diag >= 0) {
-    // class tables: tab[off_c + p] = coefficient_c (count_c - 2 p), p = the
-    // number of class-c terms with odd parity at an index
-    for (int c = 0, off = 0; c < X.dcls; off += X.dcount[c] + 1, c++)
-      for (int p = tid; p <= X.dcount[c]; p += BLOCK)
-        tab[off + p] = X.terms[X.dfirst[c]].c * (double)(X.dcount[c] - 2 * p);
-  }
-  if (X.tables && X.diag >= 0) {
-    // tab[c][v] = sum of the chunk-c diagonal terms c_t (-1)^popcount(v & z_t)
-    const XGroup& G = X.groups[X.diag];
-    for (int e = tid; e < nch * 256; e += BLOCK) {
-      const int c = e >> 8, v = e & 255;
-      double s = 0.0;
-      for (int t = G.first; t < G.first + G.count; t++) {
-        if (X.terms[t].chunk != c + 1) continue;
-        const uint32_t zc = (uint32_t)(X.terms[t].zg >> (EXP_CHUNK_BITS * c)) & 255u;
-        s += (__popc((uint32_t)v & zc) & 1) ? -X.terms[t].c : X.terms[t].c;
-      }
-      tab[e] = s;
-    }
-  }
+  xp_tables<BLOCK>(X, tab);
   double acc = 0.0;
   for (int p = 0; p < X.npass; p++) {
     const XPass& Q = X.passes[p];
-    const int k = Q.k, m = Q.m, kh = k - m;
+    const int k = Q.k, m = Q.m;
     const uint32_t T = 1u << k, lowmask = (1u << m) - 1u;
     __syncthreads();
-    if (tid < 32) {
-      const int kl = kh < 5 ? kh : 5;
-      hlo[tid] = tid < (1u << kl) ? (uint32_t)(deposit(tid, Q.tbits + m, kl) >> m) : 0u;
-      if (tid < (1u << (XP_TILE_BITS - XP_LOW_BITS - 5)))
-        hhi[tid] = kh > 5 ? (uint32_t)(deposit((uint64_t)tid << 5, Q.tbits + m, kh) >> m) : 0u;
-    }
+    xp_offsets(Q, hlo, hhi);
     __syncthreads();
-    auto hioff = [&](uint32_t j) { return hlo[j & 31u] | hhi[j >> 5]; };
     const uint64_t ntiles = 1ull << (n - k);
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const uint64_t base = deposit(t, Q.obits, Q.nobits);
-      const double2* __restrict__ sm = xsm;
       // the next tile of this pass (same tile index, its CTA bits) into L2:
       // one hint per run of 2^m amplitudes, at most one per 128-byte line
       const int64_t ahead =
           t + gridDim.x < ntiles ? (int64_t)(deposit(t + gridDim.x, Q.obits, Q.nobits) - base) : 0;
       const uint32_t pmask = ahead ? (1u << (m < 3 ? m : 3)) - 1u : ~0u;
       for (uint32_t s = tid; s < T; s += BLOCK) {
-        const double2* src = st + (base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask));
+        const double2* src =
+            st + (base | ((uint64_t)(hlo[(s >> m) & 31u] | hhi[(s >> m) >> 5]) << m) | (s & lowmask));
         xsm[s] = *src;
         if ((s & pmask) == 0) prefetch_l2(src + ahead);
       }
       __syncthreads();
-      for (int g = Q.g0; g < Q.g1; g++) {
-        const XGroup& G = X.groups[g];
-        if (G.mode == XG_CLASS) {
-          int ng = 1;
-          while (g + ng < Q.g1 && X.groups[g + ng].mode == XG_CLASS &&
-                 X.groups[g + ng].w == G.w && X.groups[g + ng].part == G.part &&
-                 X.groups[g + ng].coef == G.coef)
-            ng++;
-          if (G.w == 1)
-            acc += xp_class_run<BLOCK, 0>(sm, T, &G, ng, coef);
-          else if (G.w == 2)
-            acc += xp_class_run<BLOCK, 1>(sm, T, &G, ng, coef);
-          else
-            acc += xp_class_run<BLOCK, 2>(sm, T, &G, ng, coef);
-          g += ng - 1;
-        } else if (G.mode == XG_DIAG && X.dcls) {
-          // per class: count the odd parities with integer operations, read
-          // the class's sum from its table (K - 1 adds per amplitude)
-          for (uint32_t s = tid; s < T; s += BLOCK) {
-            const uint64_t gi = base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask);
-            const double2 v = sm[s];
-            const double pr = fma(v.x, v.x, v.y * v.y);
-            auto odd = [&](int c) {   // class-c terms with odd parity at gi
-              int o = 0;
-              for (int q = X.dfirst[c]; q < X.dfirst[c] + X.ddirect[c]; q++)
-                o += __popcll(gi & X.terms[q].zg) & 1;
-              for (int e = 0; e < X.dnd[c]; e++) {
-                const int dl = X.ddel[c][e];
-                o += __popcll((dl ? gi ^ (gi >> dl) : gi) & X.dmsk[c][e]);
-              }
-              return o;
-            };
-            double d = tab[odd(0)];
-            for (int c = 1, off = X.dcount[0] + 1; c < X.dcls; off += X.dcount[c] + 1, c++)
-              d += tab[off + odd(c)];
-            acc = fma(d, pr, acc);
-          }
-        } else if (G.mode == XG_DIAG) {
-          for (uint32_t s = tid; s < T; s += BLOCK) {
-            const uint64_t gi = base | ((uint64_t)hioff(s >> m) << m) | (s & lowmask);
-            const double2 v = sm[s];
-            const double pr = fma(v.x, v.x, v.y * v.y);
-            double d = 0.0;
-            if (X.tables)
-              for (int c = 0; c < nch; c++) d += tab[c * 256 + ((gi >> (EXP_CHUNK_BITS * c)) & 255)];
-            for (int q = X.tables ? G.direct : G.first; q < G.first + G.count; q++) {
-              const XTerm& Tm = X.terms[q];
-              const uint32_t f = (uint32_t)(__popcll(gi & Tm.zg) & 1) << 31;
-              d += xsign(Tm.c, f);
-            }
-            acc = fma(d, pr, acc);
-          }
-        } else {
-          // table mode: index bit q = parity(j & z_q), CTA part per tile
-          uint32_t gmask = 0, zl[XP_TABLE_TERMS];
-#pragma unroll
-          for (int q = 0; q < XP_TABLE_TERMS; q++) {
-            zl[q] = q < G.count ? X.terms[G.first + q].zl : 0u;
-            if (q < G.count) gmask |= (uint32_t)(__popcll(base & X.terms[G.first + q].zg) & 1) << q;
-          }
-          const uint32_t x = G.x;
-          const int h = G.h;
-          const double2* __restrict__ C = coef + G.coef;
-          const int part = G.part;
-          for (uint32_t j = tid; j < (T >> 1); j += BLOCK) {
-            const uint32_t i0 = insert0(j, h), j0 = i0 ^ x;
-            const double2 A = sm[i0], B = sm[j0];
-            uint32_t idx = gmask;
-#pragma unroll
-            for (int q = 0; q < XP_TABLE_TERMS; q++) idx ^= (uint32_t)(__popc(j0 & zl[q]) & 1) << q;
-            const double2 w = C[idx];
-            if (part != 2) acc = fma(w.x, fma(A.x, B.x, A.y * B.y), acc);
-            if (part != 1) acc = fma(w.y, fma(A.x, B.y, -(A.y * B.x)), acc);
-          }
-        }
-      }
+      acc += xp_tile<BLOCK>(xsm, T, X, Q, base, hlo, hhi, coef, tab);
       __syncthreads();
     }
   }

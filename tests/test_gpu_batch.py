@@ -65,6 +65,20 @@ def test_batched_psr_n16_ring(lq):
     np.testing.assert_allclose(g, g_w, rtol=0, atol=RTOL * max(1.0, np.abs(g_w).max()))
 
 
+@pytest.mark.parametrize("n,depth,kind", [(13, 3, "ring"), (14, 2, "ladder")])
+def test_batched_psr_tiled_multilayer(lq, n, depth, kind):
+    # states wider than the 2^12 shared-memory tile run as tile passes over a
+    # scratch state; several layers let the phases sink across passes, and
+    # every shifted circuit's patch must still reach its own gate's factor
+    gates, P = W.hea(n, depth, kind)
+    th = W.angles(P, 40 + n)
+    terms = W.heisenberg(n, ring=kind == "ring")
+    e_w, g_w = oracle.param_shift(n, gates, th, terms)
+    e, g = lq.param_shift_grad(n, gates, th, terms, method=lq.PSR_BATCHED)
+    assert abs(e - e_w) <= RTOL * max(1, abs(e_w))
+    np.testing.assert_allclose(g, g_w, rtol=0, atol=RTOL * max(1.0, np.abs(g_w).max()))
+
+
 def test_batched_after_workspace_reallocation(lq):
     """A replayed launch must follow its workspace: free the workspace and
     hand the memory back to the driver, allocate again (the address usually
