@@ -96,6 +96,19 @@ def test_n_range_and_null_pointers(L):
     assert L.lq_expval_workspace_size(10, 3) > 0
 
 
+def test_batched_workspace_sizing_on_host(L):
+    # sizing a batched launch plans every problem on the host (lowering,
+    # tile passes, the tiled <H> plan of states wider than a tile) and needs
+    # no device: without one the grid is an estimate, with one the occupancy
+    # query decides; the scratch states make the size grow with n
+    import paper_2512_23183_gb300 as lq
+
+    sizes = [L.lq_param_shift_workspace_size(n, 4 * n, 3 * (n - 1), lq.PSR_BATCHED)
+             for n in (10, 13, 16, 20)]
+    assert all(s > 0 for s in sizes), sizes
+    assert sizes == sorted(sizes) and sizes[-1] > sizes[0], sizes
+
+
 def test_probes_reject_bad_arguments_on_host(L):
     tf = ctypes.c_double()
     for fn in (L.lq_measure_fp64_fma, L.lq_measure_fp64_tile_sweep):
